@@ -1,0 +1,413 @@
+"""Benchmark: FastVPINNs loss + gradient evaluations per second on one B300.
+
+Workload (default): the precision configuration -- Poisson on the gear-like
+annulus 0.5 <= r <= 1 + 0.1 cos(12 theta), 128 x 64 O-grid (8192 quads),
+10 x 10 GLL points and 8 x 8 test functions per element (819,200 quadrature
+points), tanh MLP 2-50x4-1, 1000 Dirichlet points.  One step = one
+fv_loss_grad: network forward with tangents at every point, contraction with
+the stacked premultiplier tensor G (read from HBM once), variational +
+boundary loss, adjoint seeds, reverse sweep to the weight gradient.  The G/F
+precompute runs once per mesh and is reported separately.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--precision auto|fp32|tf32|bf16|fp64]
+
+Under torchrun (N > 1) every rank evaluates its own replica of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "loss+grad evals/s & quad-pts/s, mixed-precision fused vs plain FP32 at stated error"
+UNIT = "loss+grad evals/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6400.0), d.get("bf16_tflops", 1800.0), d.get("bf16_tflops_sustained", 1400.0), \
+            d.get("sm_max_mhz", 2032.0), "measured"
+    except Exception:
+        return 6400.0, 1800.0, 1400.0, 2032.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+def mlp_flops_per_point(widths):
+    """Forward with two tangents: 3 streams x 2 flops per weight (GEMM part)."""
+    macs = sum(widths[i] * widths[i + 1] for i in range(len(widths) - 1))
+    fwd = 3 * 2 * macs
+    # reverse: weight-gradient GEMM (3 streams) over every map + input-adjoint GEMM over maps 1..L-1
+    macs_in = sum(widths[i] * widths[i + 1] for i in range(1, len(widths) - 1))
+    bwd = 3 * 2 * macs + 3 * 2 * macs_in
+    return fwd, bwd
+
+
+def contract_bytes(mesh, gsize):
+    """Algorithmic bytes of one contraction launch: G once (no padding), F,
+    the gradient field in (u_x, u_y) and the seeds out (3 values per point)."""
+    G = mesh.n_elements * mesh.n_comp * mesh.Nt * mesh.Nq * gsize
+    F = mesh.n_elements * mesh.Nt * 8
+    return G + F + mesh.n_points * 2 * 4 + mesh.n_points * 3 * 4, G
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+def oracle_sample(prob, target_s=10.0, max_elems=None):
+    """Time the CPU FP64 oracle on the first n elements of the workload (with
+    its boundary points), growing n until one evaluation takes ~target_s/3."""
+    import fv_inputs as fi
+    import oracle
+    nth = os.cpu_count() or 1
+    n = 64
+    while True:
+        sub = fi.Problem(**{**prob.__dict__, "mesh": prob.mesh.subset(0, n)})
+        b = oracle.Bound(sub)
+        t0 = time.perf_counter()
+        b.loss_grad(prob.params, n_threads=nth)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 3 or n >= (max_elems or prob.mesh.n_elements):
+            return sub, b, dt, nth
+        n = min(prob.mesh.n_elements, int(n * max(2.0, (target_s / 3) / max(dt, 1e-3))))
+
+
+def run_reference(args, prob):
+    """The oracle as it stands on the host cores: each step one loss+grad of a
+    bounded element sample of the workload, scaled to whole-workload evals/s."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    sub, b, _, nth = oracle_sample(prob, target_s=max(3.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        b.loss_grad(prob.params, n_threads=nth)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        b.loss_grad(prob.params, n_threads=nth)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    pts = sub.n_points + len(sub.bd_xy)
+    full = prob.n_points + len(prob.bd_xy)
+    evals = (pts / t) / full
+    sample = "%d of %d elements (%d quad + %d boundary points), FP64 oracle, %d OpenMP threads" % (
+        sub.mesh.n_elements, prob.mesh.n_elements, sub.n_points, len(sub.bd_xy), nth)
+    line = {"impl": "reference", "metric": METRIC, "value": evals, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full / (pts / t),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": prob.name, "quad_points": prob.n_points,
+                                            "elements": prob.mesh.n_elements, "Q": prob.quad_order,
+                                            "T": prob.test_order, "mlp": "2-50x4-1"},
+            "quad_pts_per_s": pts / t,
+            "cpu_baseline": {"value": evals, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample},
+            "e2e": {"value": evals, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def time_steps(torch, stream, fn, steps):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    import fv_inputs as fi
+    prob = fi.config3_annulus()
+    if args.impl == "reference":
+        return run_reference(args, prob)
+
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2404_12063_b300 import api
+    from paper_2404_12063_b300 import _native as N
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(local, stream)
+
+    variants = ["fp32"]
+    if args.precision != "auto":
+        variants = [args.precision]
+    else:
+        for p in ("bf16", "tf32"):
+            try:
+                pb_try = api.problem_from_inputs(ctx, fi.config1_tiny(), p)
+                pb_try.loss_grad(torch.tensor(fi.config1_tiny().params, dtype=torch.float32, device="cuda"))
+                variants.append(p)
+            except Exception:
+                pass
+
+    # G / F precompute (a1), timed once
+    t0 = time.perf_counter()
+    torch.cuda.synchronize()
+    meshes = {}
+    for st in ("fp32", "bf16"):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        meshes[st] = api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, prob.quad_order, prob.test_order, st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        meshes[st + "_ms"] = ev0.elapsed_time(ev1)
+    build_wall = time.perf_counter() - t0
+
+    hbm, bf16_peak, bf16_sus, sm_max, peak_kind = peaks()
+    fwd_fl, bwd_fl = mlp_flops_per_point(prob.widths)
+    P_tot = prob.n_points + len(prob.bd_xy)
+    results = {}
+    for v in variants:
+        storage = "bf16" if v == "bf16" else "fp32"
+        pb = api.problem_from_inputs(ctx, prob, v, storage=storage, mesh=meshes[storage])
+        params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+        grad = torch.empty_like(params)
+        out = torch.zeros(5, dtype=torch.float64, device="cuda")
+        fn = lambda: pb.loss_grad(params, grad, out)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms = time_steps(torch, stream, fn, args.steps)
+        cl = clocks.stop()
+        ms = max_over_ranks(ms, world, torch.device("cuda", local))
+        # per-kernel times over a second timed pass (CUDA events around each launch on this stream)
+        ctx.reset_kernel_times()
+        ctx.enable_timing(True)
+        for _ in range(args.steps):
+            fn()
+        kt = ctx.kernel_times()
+        ctx.enable_timing(False)
+        ctx.reset_kernel_times()
+        # end to end through the public API: params H2D from pinned host, loss + grad D2H
+        h_params = torch.tensor(prob.params, dtype=pb.dtype).pin_memory()
+        h_grad = torch.empty_like(h_params).pin_memory()
+        h_out = torch.empty(5, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            params.copy_(h_params, non_blocking=True)
+            pb.loss_grad(params, grad, out)
+            h_grad.copy_(grad, non_blocking=True)
+            h_out.copy_(out, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        ms_e2e = time_steps(torch, stream, e2e_step, args.steps)
+        ms_e2e = max_over_ranks(ms_e2e, world, torch.device("cuda", local))
+        results[v] = dict(ms=ms, kt=kt, clocks=cl, ms_e2e=ms_e2e, loss=float(out[0]), pb=pb,
+                          bytes_h2d=h_params.numel() * h_params.element_size(),
+                          bytes_d2h=h_grad.numel() * h_grad.element_size() + 5 * 8)
+
+    # error of each variant vs the GPU FP64 path (itself parity-tested against the oracle)
+    ref64 = api.problem_from_inputs(ctx, prob, "fp64")
+    p64 = torch.tensor(prob.params, dtype=torch.float64, device="cuda")
+    o64, g64 = ref64.loss_grad(p64)
+    o64, g64 = o64.clone(), g64.clone()
+    for v, r in results.items():
+        p = torch.tensor(prob.params, dtype=r["pb"].dtype, device="cuda")
+        o, g = r["pb"].loss_grad(p)
+        r["err_loss"] = abs(float(o[0]) - float(o64[0])) / abs(float(o64[0]))
+        r["err_grad"] = float(torch.linalg.norm(g.double() - g64) / torch.linalg.norm(g64))
+    del ref64
+
+    # headline: the fastest variant within its stated tolerance
+    tol = {"fp32": 1e-5, "tf32": 2e-2, "bf16": 2e-2, "fp64": 1e-10}
+    ok = [v for v in results if results[v]["err_loss"] < tol[v] and results[v]["err_grad"] < tol[v]]
+    head = min(ok or list(results), key=lambda v: results[v]["ms"])
+    r = results[head]
+    evals = world * 1e3 / r["ms"]
+
+    # roofline of the dominant kernel and of the G stream
+    def kavg(name):
+        t = r["kt"].get(name)
+        return (t[0] / t[1]) if t else None
+
+    mesh = meshes["bf16" if head == "bf16" else "fp32"]
+    cbytes, gbytes = contract_bytes(mesh, 2 if head == "bf16" else 4)
+    tc = head in ("bf16", "tf32")
+    kinds = {k: v for k, v in r["kt"].items()}
+    dom = max(kinds, key=lambda k: kinds[k][0]) if kinds else None
+    c_ms = kavg("contract")
+    g_roof = None
+    if c_ms:
+        ach = cbytes / (c_ms * 1e-3) / 1e9
+        g_roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                  "traffic": None, "kernel": "contract", "algorithmic_bytes": cbytes, "g_bytes": gbytes,
+                  "frac_of_8TBps": ach / 8000.0, "peak_kind": peak_kind + " (copy)"}
+    roof = None
+    if dom in ("mlp_bwd", "mlp_fwd", "mlp_bwd_tc", "mlp_fwd_tc"):
+        fl = (bwd_fl if "bwd" in dom else fwd_fl) * P_tot
+        ach = fl / (kavg(dom) * 1e-3) / 1e12
+        if tc:
+            pk = bf16_sus if head == "bf16" else bf16_sus / 2
+            roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "kernel": dom, "peak_kind": peak_kind + " sustained bf16" +
+                    ("" if head == "bf16" else " x 1/2 (tf32 nominal ratio)")}
+        else:
+            pk = 148 * 128 * 2 * sm_max * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "kernel": dom,
+                    "peak_kind": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x %.0f MHz" % sm_max}
+    elif g_roof:
+        roof = g_roof
+
+    launches_per_step = sum(v[1] for v in r["kt"].values()) / args.steps if r["kt"] else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sub, b, dt, nth = oracle_sample(prob, target_s=10.0)
+        pts = sub.n_points + len(sub.bd_xy)
+        cpu = {"value": (pts / dt) / P_tot, "unit": UNIT, "cores": nth, "kind": "oracle",
+               "sample": "%d of %d elements (%d quad + %d boundary points), one FP64 loss+grad, %.2f s"
+                         % (sub.mesh.n_elements, prob.mesh.n_elements, sub.n_points, len(sub.bd_xy), dt),
+               "quad_pts_per_s": pts / dt}
+
+    variants_out = {}
+    for v, rr in results.items():
+        variants_out[v] = {"evals_per_s": world * 1e3 / rr["ms"], "ms_per_step": rr["ms"],
+                           "quad_pts_per_s": world * prob.n_points * 1e3 / rr["ms"],
+                           "rel_err_loss_vs_fp64": rr["err_loss"], "rel_err_grad_vs_fp64": rr["err_grad"],
+                           "kernel_ms": {k: v2[0] / v2[1] for k, v2 in rr["kt"].items()}}
+    line = {
+        "metric": METRIC, "value": evals, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32/f32-accum", "bf16": "bf16/f32-accum",
+                                       "fp64": "f64"}[head],
+        "data": "synthetic",
+        "config": {"workload": prob.name, "elements": prob.mesh.n_elements, "Q": prob.quad_order,
+                   "T": prob.test_order, "quad_points": prob.n_points, "boundary_points": len(prob.bd_xy),
+                   "mlp": "2-50x4-1", "variant": head, "g_storage": "bf16" if head == "bf16" else "fp32",
+                   "l2": "inputs larger than L2 (G = %.0f MB)" % (gbytes / 1e6), "parallelism": "replicas"},
+        "quad_pts_per_s": world * prob.n_points * 1e3 / r["ms"],
+        "variants": variants_out,
+        "g_build_ms": {"fp32": meshes["fp32_ms"], "bf16": meshes["bf16_ms"]},
+        "clocks": r["clocks"],
+        "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": UNIT, "h2d_bytes_per_step": r["bytes_h2d"],
+                "d2h_bytes_per_step": r["bytes_d2h"]},
+        "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
+        "gpu_launches_per_step": launches_per_step,
+        "roofline": roof,
+        "roofline_g_stream": g_roof,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,550 @@
+// C ABI: contexts, workspace, evaluation entry points, Adam, batches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+#include "fv_internal.cuh"
+
+namespace fv {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+bool make_shape(const fv_mlp_desc* d, MlpShape* s) {
+  if (!d || !d->widths || d->n_layers < 2 || d->n_layers > kMaxLayers) return false;
+  if (d->widths[0] != 2 || d->widths[d->n_layers] != 1) return false;
+  s->L = d->n_layers;
+  int o = 0;
+  for (int i = 0; i <= d->n_layers; ++i) {
+    const int w = d->widths[i];
+    if (i > 0 && i < d->n_layers && (w < 1 || w > kMaxWidth)) return false;
+    s->w[i] = w;
+  }
+  for (int i = 0; i < d->n_layers; ++i) { s->off[i] = o; o += s->w[i + 1] * s->w[i] + s->w[i + 1]; }
+  s->n_params = o;
+  return true;
+}
+
+int ws_reserve(fv_ctx ctx, size_t bytes, void** out) {
+  if (ctx->ws.bytes < bytes) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaFree(ctx->ws.ptr);
+    ctx->ws.ptr = nullptr; ctx->ws.bytes = 0;
+    const size_t want = std::max(bytes, (size_t)(1 << 20));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ws.ptr, want);
+    if (e != cudaSuccess) {
+      set_error("workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;
+    }
+    ctx->ws.bytes = want;
+  }
+  *out = ctx->ws.ptr;
+  return FV_OK;
+}
+
+static cudaEvent_t get_event(fv_ctx ctx) {
+  if (!ctx->free_events.empty()) {
+    cudaEvent_t e = ctx->free_events.back();
+    ctx->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void time_begin(fv_ctx ctx, int kind, cudaEvent_t* a) {
+  (void)kind;
+  *a = nullptr;
+  if (!ctx->timing) return;
+  *a = get_event(ctx);
+  cudaEventRecord(*a, ctx->stream);
+}
+
+void time_end(fv_ctx ctx, int kind, cudaEvent_t a) {
+  if (!ctx->timing || !a) return;
+  cudaEvent_t b = get_event(ctx);
+  cudaEventRecord(b, ctx->stream);
+  ctx->recs.push_back({kind, a, b});
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t al(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Boundary and sensor terms (Sec. 2.2 L_b, Sec. 4.7 L_s) and their seeds.
+template <class R>
+__global__ void bc_kernel(const double* __restrict__ val, int n_bd, int n_s, double tau, double gamma,
+                          const R* __restrict__ U, R* __restrict__ UB, int64_t P_mesh, int64_t P_tot,
+                          double* __restrict__ partial2) {
+  __shared__ double red[256 * 4];
+  KSum lb, ls;
+  for (int d = threadIdx.x; d < n_bd + n_s; d += blockDim.x) {
+    const int64_t gp = P_mesh + d;
+    const double diff = (double)U[gp] - val[d];
+    double seed;
+    if (d < n_bd) { lb.add(diff * diff); seed = 2.0 * tau * diff / n_bd; }
+    else { ls.add(diff * diff); seed = 2.0 * gamma * diff / n_s; }
+    if (UB) {
+      UB[gp] = (R)seed;
+      UB[P_tot + gp] = (R)0;
+      UB[2 * P_tot + gp] = (R)0;
+    }
+  }
+  red[threadIdx.x * 4 + 0] = lb.s; red[threadIdx.x * 4 + 1] = lb.c;
+  red[threadIdx.x * 4 + 2] = ls.s; red[threadIdx.x * 4 + 3] = ls.c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    KSum a, b;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      a.add(red[t * 4]); a.add(red[t * 4 + 1]);
+      b.add(red[t * 4 + 2]); b.add(red[t * 4 + 3]);
+    }
+    partial2[0] = a.value();
+    partial2[1] = b.value();
+  }
+}
+
+// Deterministic final sums: gradient over per-CTA partials (fixed order) and
+// the loss scalars.  out = (L, Lv, Lb, Ls, dL/deps).
+template <class R>
+__global__ void finalize_kernel(const double* __restrict__ cpart, int n_cpart, const double* __restrict__ bcpart,
+                                const double* __restrict__ gpart, int n_gpart, int n_params, double inv_norm,
+                                double tau, double gamma, int n_bd, int n_s, R* __restrict__ grad,
+                                double* __restrict__ out) {
+  if (grad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_params; i += gridDim.x * blockDim.x) {
+      double s = 0.0;
+      for (int b = 0; b < n_gpart; ++b) s += gpart[(size_t)b * n_params + i];
+      grad[i] = (R)s;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    KSum l, d;
+    for (int b = 0; b < n_cpart; ++b) { l.add(cpart[2 * b]); d.add(cpart[2 * b + 1]); }
+    const double Lv = inv_norm * l.value();
+    const double Lb = n_bd ? bcpart[0] / n_bd : 0.0;
+    const double Ls = n_s ? bcpart[1] / n_s : 0.0;
+    out[0] = Lv + tau * Lb + gamma * Ls;
+    out[1] = Lv;
+    out[2] = Lb;
+    out[3] = Ls;
+    out[4] = d.value();
+  }
+}
+
+template <class R>
+__global__ void adam_kernel(R* __restrict__ p, const R* __restrict__ g, int64_t n, R* __restrict__ m,
+                            R* __restrict__ v, double* eps_p, const double* dLde, double* me, int with_eps, int* t,
+                            double lr, double b1, double b2, double ae) {
+  const int tt = *t + 1;
+  const double c1 = 1.0 - pow(b1, (double)tt), c2 = 1.0 - pow(b2, (double)tt);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double gi = (double)g[i];
+    const double mi = b1 * (double)m[i] + (1.0 - b1) * gi;
+    const double vi = b2 * (double)v[i] + (1.0 - b2) * gi * gi;
+    m[i] = (R)mi; v[i] = (R)vi;
+    p[i] = (R)((double)p[i] - lr * (mi / c1) / (sqrt(vi / c2) + ae));
+  }
+  if (with_eps && threadIdx.x == 0) {
+    const double gi = dLde[0];
+    const double mi = b1 * me[0] + (1.0 - b1) * gi;
+    const double vi = b2 * me[1] + (1.0 - b2) * gi * gi;
+    me[0] = mi; me[1] = vi;
+    eps_p[0] -= lr * (mi / c1) / (sqrt(vi / c2) + ae);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *t = tt;
+}
+
+int check_eval(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp, const void* params,
+               const fv_eval_opts* opts, MlpShape* sh) {
+  FV_CHECK_ARG(ctx && mesh && forcing && mlp && params && opts, "evaluation: null argument");
+  FV_CHECK_ARG(forcing->mesh == mesh, "evaluation: forcing was assembled on a different mesh");
+  FV_CHECK_ARG(mesh->ctx == ctx && (!bc || bc->ctx == ctx), "evaluation: handles belong to another context");
+  FV_CHECK_ARG(opts->norm == FV_NORM_TEST || opts->norm == FV_NORM_ELEM, "evaluation: bad norm");
+  if (!make_shape(mlp, sh)) {
+    set_error("network shape unsupported: need widths[0]=2, widths[L]=1, 2..%d affine maps, hidden widths 1..%d",
+              kMaxLayers, kMaxWidth);
+    return FV_ERR_UNSUPPORTED;
+  }
+  const fv_precision p = opts->mlp_precision;
+  if (p != FV_FP64 && p != FV_FP32 && p != FV_TF32 && p != FV_BF16) {
+    set_error("evaluation: unknown precision");
+    return FV_ERR_UNSUPPORTED;
+  }
+  if (p == FV_FP64 && mesh->storage != FV_FP64) {
+    set_error("FP64 evaluation needs a mesh built with FV_FP64 storage");
+    return FV_ERR_UNSUPPORTED;
+  }
+  if ((opts->bx != 0.0 || opts->by != 0.0) && mesh->n_comp != 3) {
+    set_error("non-zero convection needs a mesh built with with_mass_term=1");
+    return FV_ERR_ARG;
+  }
+  return FV_OK;
+}
+
+struct WsLayout {
+  size_t U, UB, cpart, bcpart, gpart, total;
+};
+
+// The core evaluation shared by fv_loss, fv_loss_grad and fv_inverse_step.
+int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp, const void* params,
+             const fv_eval_opts* opts, const double* eps_dev, bool want_grad, void* grad, double* out,
+             void* U_copy = nullptr, void* UB_copy = nullptr, double* R_out = nullptr) {
+  MlpShape sh;
+  int rc = check_eval(ctx, mesh, forcing, bc, mlp, params, opts, &sh);
+  if (rc) return rc;
+  EvalPlan pl;
+  pl.shape = sh;
+  pl.prec = opts->mlp_precision;
+  pl.P_mesh = mesh->P;
+  pl.n_bd = bc ? bc->n_bd : 0;
+  pl.n_s = bc ? bc->n_s : 0;
+  pl.P_tot = pl.P_mesh + pl.n_bd + pl.n_s;
+  pl.want_grad = want_grad;
+  const bool tc = pl.prec == FV_TF32 || pl.prec == FV_BF16;
+  if (tc && !tc_supported(pl)) {
+    set_error("tensor-core path does not support this network shape");
+    return FV_ERR_UNSUPPORTED;
+  }
+  const size_t rsz = pl.prec == FV_FP64 ? 8 : 4;
+  int cgrid, E, S;
+  size_t csmem;
+  contract_grid(ctx, mesh, pl.prec, &cgrid, &E, &S, &csmem);
+  int nb = 0;
+  if (want_grad) {
+    nb = tc ? mlp_bwd_tc_blocks(ctx, pl) : mlp_bwd_blocks(ctx, pl);
+    if (nb <= 0) return nb < 0 ? -nb : FV_ERR_UNSUPPORTED;
+  }
+  WsLayout w;
+  size_t o = 0;
+  w.U = o; o += al(3 * pl.P_tot * rsz);
+  w.UB = o; o += want_grad ? al(3 * pl.P_tot * rsz) : 0;
+  w.cpart = o; o += al(2 * (size_t)cgrid * 8);
+  w.bcpart = o; o += al(2 * 8);
+  w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
+  w.total = o;
+  void* base;
+  rc = ws_reserve(ctx, w.total, &base);
+  if (rc) return rc;
+  char* b = static_cast<char*>(base);
+  void* U = b + w.U;
+  void* UB = want_grad ? b + w.UB : nullptr;
+  double* cpart = reinterpret_cast<double*>(b + w.cpart);
+  double* bcpart = reinterpret_cast<double*>(b + w.bcpart);
+  double* gpart = reinterpret_cast<double*>(b + w.gpart);
+  const double* Xe = bc ? bc->xy : nullptr;
+
+  rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U) : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
+  if (rc) return rc;
+  const double inv_norm = 1.0 / (opts->norm == FV_NORM_TEST ? mesh->Nt : mesh->n_e);
+  int ncp = 0;
+  rc = launch_contract(ctx, mesh, forcing, pl, U, UB, opts->eps, eps_dev ? eps_dev : opts->eps_dev, opts->bx, opts->by,
+                       2.0 * inv_norm, cpart, &ncp, R_out);
+  if (rc) return rc;
+  if (bc && pl.n_bd + pl.n_s > 0) {
+    cudaEvent_t ta;
+    time_begin(ctx, K_BC, &ta);
+    if (pl.prec == FV_FP64)
+      bc_kernel<double><<<1, 256, 0, ctx->stream>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const double*)U,
+                                                   (double*)UB, pl.P_mesh, pl.P_tot, bcpart);
+    else
+      bc_kernel<float><<<1, 256, 0, ctx->stream>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const float*)U,
+                                                  (float*)UB, pl.P_mesh, pl.P_tot, bcpart);
+    time_end(ctx, K_BC, ta);
+    FV_CUDA_TRY(cudaGetLastError());
+  } else {
+    FV_CUDA_TRY(cudaMemsetAsync(bcpart, 0, 16, ctx->stream));
+  }
+  if (U_copy) FV_CUDA_TRY(cudaMemcpyAsync(U_copy, U, 3 * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (UB_copy && UB)
+    FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, 3 * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
+  int ngp = 0;
+  if (want_grad) {
+    rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp)
+            : launch_mlp_bwd(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp);
+    if (rc) return rc;
+  }
+  cudaEvent_t ta;
+  time_begin(ctx, K_FINALIZE, &ta);
+  const double tau = bc ? bc->tau : 0.0, gamma = bc ? bc->gamma : 0.0;
+  const int fgrid = want_grad ? std::max(1, std::min(ctx->n_sm, (sh.n_params + 255) / 256)) : 1;
+  if (pl.prec == FV_FP64)
+    finalize_kernel<double><<<fgrid, 256, 0, ctx->stream>>>(cpart, ncp, bcpart, gpart, ngp, sh.n_params, inv_norm, tau,
+                                                            gamma, pl.n_bd, pl.n_s, (double*)grad, out);
+  else
+    finalize_kernel<float><<<fgrid, 256, 0, ctx->stream>>>(cpart, ncp, bcpart, gpart, ngp, sh.n_params, inv_norm, tau,
+                                                           gamma, pl.n_bd, pl.n_s, (float*)grad, out);
+  time_end(ctx, K_FINALIZE, ta);
+  FV_CUDA_TRY(cudaGetLastError());
+  return FV_OK;
+}
+
+}  // namespace
+}  // namespace fv
+
+using namespace fv;
+
+extern "C" const char* fv_last_error(void) { return fv::g_err; }
+
+extern "C" int fv_ctx_create(fv_ctx* out, int device, void* stream) {
+  clear_error();
+  FV_CHECK_ARG(out, "fv_ctx_create: null output");
+  int n = 0;
+  FV_CUDA_TRY(cudaGetDeviceCount(&n));
+  FV_CHECK_ARG(device >= 0 && device < n, "fv_ctx_create: device %d out of range (%d devices)", device, n);
+  FV_CUDA_TRY(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  FV_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+  if (prop.major < 10) {
+    set_error("fv_ctx_create: device %d is sm_%d%d; this library is built for sm_103a", device, prop.major, prop.minor);
+    return FV_ERR_UNSUPPORTED;
+  }
+  fv_ctx c = new fv_ctx_s();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->n_sm = prop.multiProcessorCount;
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  cudaError_t e = cudaMalloc(&c->err_dev, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    delete c;
+    set_error("fv_ctx_create: %s", cudaGetErrorString(e));
+    return FV_ERR_CUDA;
+  }
+  *out = c;
+  return FV_OK;
+}
+
+extern "C" int fv_ctx_set_stream(fv_ctx ctx, void* stream) {
+  clear_error();
+  FV_CHECK_ARG(ctx, "fv_ctx_set_stream: null context");
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return FV_OK;
+}
+
+extern "C" int fv_ctx_destroy(fv_ctx ctx) {
+  clear_error();
+  if (!ctx) return FV_OK;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->free_events) cudaEventDestroy(e);
+  cudaFree(ctx->ws.ptr);
+  cudaFree(ctx->err_dev);
+  delete ctx;
+  return FV_OK;
+}
+
+extern "C" int fv_ctx_enable_timing(fv_ctx ctx, int on) {
+  clear_error();
+  FV_CHECK_ARG(ctx, "fv_ctx_enable_timing: null context");
+  ctx->timing = on != 0;
+  return FV_OK;
+}
+
+static void drain_times(fv_ctx ctx) {
+  for (auto& r : ctx->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ctx->kind_ms[r.kind] += ms;
+      ctx->kind_launches[r.kind] += 1;
+    }
+    ctx->free_events.push_back(r.a);
+    ctx->free_events.push_back(r.b);
+  }
+  ctx->recs.clear();
+}
+
+extern "C" int fv_ctx_kernel_times(fv_ctx ctx, int max_kinds, double* ms, int64_t* launches, int* n_kinds) {
+  clear_error();
+  FV_CHECK_ARG(ctx && ms && launches && n_kinds, "fv_ctx_kernel_times: null argument");
+  FV_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  drain_times(ctx);
+  const int n = std::min<int>(max_kinds, K_NUM_KINDS);
+  for (int i = 0; i < n; ++i) { ms[i] = ctx->kind_ms[i]; launches[i] = ctx->kind_launches[i]; }
+  *n_kinds = K_NUM_KINDS;
+  return FV_OK;
+}
+
+extern "C" int fv_ctx_reset_kernel_times(fv_ctx ctx) {
+  clear_error();
+  FV_CHECK_ARG(ctx, "fv_ctx_reset_kernel_times: null context");
+  FV_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  drain_times(ctx);
+  for (int i = 0; i < K_NUM_KINDS; ++i) { ctx->kind_ms[i] = 0; ctx->kind_launches[i] = 0; }
+  return FV_OK;
+}
+
+extern "C" const char* fv_kernel_name(int kind) {
+  static const char* names[K_NUM_KINDS] = {"g_build", "forcing", "mlp_fwd", "contract", "bc_seed", "mlp_bwd",
+                                           "finalize", "adam", "mlp_fwd_tc", "mlp_bwd_tc", "batch"};
+  return (kind >= 0 && kind < K_NUM_KINDS) ? names[kind] : "";
+}
+
+extern "C" int fv_loss(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                       const void* params, const fv_eval_opts* opts, double* out) {
+  clear_error();
+  FV_CHECK_ARG(out, "fv_loss: null output");
+  if (ctx) FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  return evaluate(ctx, mesh, forcing, bc, mlp, params, opts, nullptr, false, nullptr, out);
+}
+
+extern "C" int fv_loss_grad(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                            const void* params, const fv_eval_opts* opts, void* grad, double* out) {
+  clear_error();
+  FV_CHECK_ARG(out && grad, "fv_loss_grad: null output");
+  if (ctx) FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  return evaluate(ctx, mesh, forcing, bc, mlp, params, opts, nullptr, true, grad, out);
+}
+
+extern "C" int fv_eval_intermediates(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                                     const void* params, const fv_eval_opts* opts, void* U_dev, void* UB_dev,
+                                     double* R_dev, double* out_dev) {
+  clear_error();
+  FV_CHECK_ARG(out_dev, "fv_eval_intermediates: null output");
+  if (ctx) FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  // the gradient goes to the workspace-backed scratch of a throw-away buffer
+  MlpShape sh;
+  if (!make_shape(mlp, &sh)) { set_error("fv_eval_intermediates: unsupported network shape"); return FV_ERR_UNSUPPORTED; }
+  void* g = nullptr;
+  FV_CUDA_TRY(cudaMalloc(&g, (size_t)sh.n_params * 8));
+  int rc = evaluate(ctx, mesh, forcing, bc, mlp, params, opts, nullptr, true, g, out_dev, U_dev, UB_dev, R_dev);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(g);
+  if (rc) return rc;
+  if (e != cudaSuccess) { set_error("fv_eval_intermediates: %s", cudaGetErrorString(e)); return FV_ERR_CUDA; }
+  return FV_OK;
+}
+
+extern "C" int fv_mlp_eval(fv_ctx ctx, const fv_mlp_desc* mlp, const void* params, fv_precision prec, int n,
+                           const double* xy, void* out) {
+  clear_error();
+  FV_CHECK_ARG(ctx && mlp && params && xy && out && n >= 0, "fv_mlp_eval: bad argument");
+  MlpShape sh;
+  if (!make_shape(mlp, &sh)) { set_error("fv_mlp_eval: unsupported network shape"); return FV_ERR_UNSUPPORTED; }
+  if (prec != FV_FP64 && prec != FV_FP32) { set_error("fv_mlp_eval: FP64 or FP32 only"); return FV_ERR_UNSUPPORTED; }
+  if (n == 0) return FV_OK;
+  FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  EvalPlan pl;
+  pl.shape = sh; pl.prec = prec; pl.P_mesh = n; pl.P_tot = n;
+  return launch_mlp_fwd(ctx, pl, params, xy, nullptr, out);
+}
+
+extern "C" int fv_adam_create(fv_ctx ctx, int64_t n, fv_precision prec, double b1, double b2, double ae, int with_eps,
+                              fv_adam* out) {
+  clear_error();
+  FV_CHECK_ARG(ctx && out && n > 0, "fv_adam_create: bad argument");
+  FV_CHECK_ARG(prec == FV_FP64 || prec == FV_FP32 || prec == FV_TF32 || prec == FV_BF16, "fv_adam_create: precision");
+  FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  fv_adam a = new fv_adam_s();
+  a->ctx = ctx; a->n = n; a->prec = prec == FV_FP64 ? FV_FP64 : FV_FP32;
+  a->beta1 = b1; a->beta2 = b2; a->eps = ae; a->with_eps = with_eps;
+  const size_t es = a->prec == FV_FP64 ? 8 : 4;
+  cudaError_t e;
+  if ((e = cudaMalloc(&a->m, es * n)) || (e = cudaMalloc(&a->v, es * n)) || (e = cudaMalloc(&a->me, 16)) ||
+      (e = cudaMalloc(&a->t, sizeof(int))) || (e = cudaMemsetAsync(a->m, 0, es * n, ctx->stream)) ||
+      (e = cudaMemsetAsync(a->v, 0, es * n, ctx->stream)) || (e = cudaMemsetAsync(a->me, 0, 16, ctx->stream)) ||
+      (e = cudaMemsetAsync(a->t, 0, sizeof(int), ctx->stream)) || (e = cudaStreamSynchronize(ctx->stream))) {
+    cudaFree(a->m); cudaFree(a->v); cudaFree(a->me); cudaFree(a->t);
+    delete a;
+    set_error("fv_adam_create: %s", cudaGetErrorString(e));
+    return FV_ERR_OOM;
+  }
+  *out = a;
+  return FV_OK;
+}
+
+extern "C" int fv_adam_destroy(fv_adam a) {
+  clear_error();
+  if (!a) return FV_OK;
+  cudaFree(a->m); cudaFree(a->v); cudaFree(a->me); cudaFree(a->t);
+  delete a;
+  return FV_OK;
+}
+
+extern "C" int fv_inverse_step(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                               void* params, double* eps_dev, const fv_eval_opts* opts, fv_adam adam, double lr,
+                               void* grad, double* out) {
+  clear_error();
+  FV_CHECK_ARG(eps_dev && grad && out, "fv_inverse_step: null argument");
+  FV_CHECK_ARG(lr <= 0.0 || adam, "fv_inverse_step: an Adam state is needed when lr > 0");
+  if (ctx) FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  int rc = evaluate(ctx, mesh, forcing, bc, mlp, params, opts, eps_dev, true, grad, out);
+  if (rc || lr <= 0.0) return rc;
+  MlpShape sh;
+  make_shape(mlp, &sh);
+  FV_CHECK_ARG(adam->n == sh.n_params && adam->ctx == ctx, "fv_inverse_step: Adam state does not match");
+  FV_CHECK_ARG((adam->prec == FV_FP64) == (opts->mlp_precision == FV_FP64), "fv_inverse_step: Adam precision");
+  cudaEvent_t ta;
+  time_begin(ctx, K_ADAM, &ta);
+  if (adam->prec == FV_FP64)
+    adam_kernel<double><<<1, 1024, 0, ctx->stream>>>((double*)params, (const double*)grad, adam->n, (double*)adam->m,
+                                                     (double*)adam->v, eps_dev, out + 4, adam->me, adam->with_eps,
+                                                     adam->t, lr, adam->beta1, adam->beta2, adam->eps);
+  else
+    adam_kernel<float><<<1, 1024, 0, ctx->stream>>>((float*)params, (const float*)grad, adam->n, (float*)adam->m,
+                                                    (float*)adam->v, eps_dev, out + 4, adam->me, adam->with_eps,
+                                                    adam->t, lr, adam->beta1, adam->beta2, adam->eps);
+  time_end(ctx, K_ADAM, ta);
+  FV_CUDA_TRY(cudaGetLastError());
+  return FV_OK;
+}
+
+// ---------------------------------------------------------------- batches
+struct fv_batch_s {
+  fv_ctx ctx;
+  std::vector<fv_instance> inst;
+  fv_mlp_desc mlp;
+  std::vector<int> widths;
+  fv_eval_opts opts;
+};
+
+extern "C" int fv_batch_plan(fv_ctx ctx, int n, const fv_instance* inst, const fv_mlp_desc* mlp,
+                             const fv_eval_opts* opts, fv_batch* out) {
+  clear_error();
+  FV_CHECK_ARG(ctx && inst && mlp && opts && out && n >= 1, "fv_batch_plan: bad argument");
+  MlpShape sh;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_eval(ctx, inst[i].mesh, inst[i].forcing, inst[i].bc, mlp, inst[i].params_dev, opts, &sh);
+    if (rc) return rc;
+    FV_CHECK_ARG(inst[i].grad_dev && inst[i].out_dev, "fv_batch_plan: instance %d has no outputs", i);
+  }
+  fv_batch b = new fv_batch_s();
+  b->ctx = ctx;
+  b->inst.assign(inst, inst + n);
+  b->widths.assign(mlp->widths, mlp->widths + mlp->n_layers + 1);
+  b->mlp.n_layers = mlp->n_layers;
+  b->mlp.widths = b->widths.data();
+  b->opts = *opts;
+  *out = b;
+  return FV_OK;
+}
+
+extern "C" int fv_batch_loss_grad(fv_batch b) {
+  clear_error();
+  FV_CHECK_ARG(b, "fv_batch_loss_grad: null batch");
+  FV_CUDA_TRY(cudaSetDevice(b->ctx->device));
+  for (auto& in : b->inst) {
+    int rc = evaluate(b->ctx, in.mesh, in.forcing, in.bc, &b->mlp, in.params_dev, &b->opts, nullptr, true, in.grad_dev,
+                      in.out_dev);
+    if (rc) return rc;
+  }
+  return FV_OK;
+}
+
+extern "C" int fv_batch_destroy(fv_batch b) {
+  clear_error();
+  delete b;
+  return FV_OK;
+}

@@ -1,0 +1,196 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fastvpinn.h"
+
+namespace fv {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define FV_CUDA_TRY(call)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      ::fv::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, \
+                      __LINE__);                                                       \
+      return _e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;               \
+    }                                                                                  \
+  } while (0)
+
+#define FV_CHECK_ARG(cond, ...)         \
+  do {                                  \
+    if (!(cond)) {                      \
+      ::fv::set_error(__VA_ARGS__);     \
+      return FV_ERR_ARG;                \
+    }                                   \
+  } while (0)
+
+// ------------------------------------------------------------------ limits
+constexpr int kMaxLayers = 12;     // affine maps
+constexpr int kMaxWidth = 128;     // hidden width
+constexpr int kMaxQ = 32;
+constexpr int kMaxT = 16;
+
+// Kernel kinds for the optional per-kernel event timing.
+enum KernelKind {
+  K_G_BUILD = 0, K_FORCING, K_MLP_FWD, K_CONTRACT, K_BC, K_MLP_BWD, K_FINALIZE, K_ADAM,
+  K_MLP_FWD_TC, K_MLP_BWD_TC, K_BATCH, K_NUM_KINDS
+};
+
+// Network shape passed to kernels by value.
+struct MlpShape {
+  int L;                        // affine maps
+  int w[kMaxLayers + 1];        // widths
+  int off[kMaxLayers];          // flat offset of W_i (b_i follows at off + w[i+1]*w[i])
+  int n_params;
+};
+
+bool make_shape(const fv_mlp_desc* d, MlpShape* s);
+
+// ------------------------------------------------------------------ handles
+struct TimingRec { int kind; cudaEvent_t a, b; };
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace fv
+
+struct fv_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_sm = 148;
+  size_t smem_optin = 227 * 1024;
+  fv::Workspace ws;
+  int* err_dev = nullptr;           // device error word (bounded waits, degenerate elements)
+  bool timing = false;
+  std::vector<fv::TimingRec> recs;
+  std::vector<cudaEvent_t> free_events;
+  double kind_ms[fv::K_NUM_KINDS] = {0};
+  int64_t kind_launches[fv::K_NUM_KINDS] = {0};
+};
+
+struct fv_mesh_s {
+  fv_ctx ctx = nullptr;
+  int n_e = 0, Q = 0, T = 0, Nq = 0, Nt = 0, n_comp = 2;
+  int64_t P = 0;
+  fv_precision storage = FV_FP32;
+  void* G = nullptr;                // [n_e] blocks of g_stride_bytes
+  size_t g_stride_bytes = 0;        // bytes per element block (16-byte multiple)
+  size_t g_elem_bytes = 0;          // bytes per element without padding
+  double* X = nullptr;              // [P][2]
+  double* tables = nullptr;         // xi[Q], w[Q], v[T][Q], dv[T][Q]
+  double* verts = nullptr;          // [n_v][2]
+  int* cells = nullptr;             // [n_e][4]
+  int n_v = 0;
+};
+
+struct fv_forcing_s {
+  fv_mesh mesh = nullptr;
+  double* F = nullptr;              // [n_e][Nt]
+};
+
+struct fv_bc_s {
+  fv_ctx ctx = nullptr;
+  int n_bd = 0, n_s = 0;
+  double* xy = nullptr;             // [n_bd + n_s][2]
+  double* val = nullptr;            // [n_bd + n_s]
+  double tau = 0, gamma = 0;
+};
+
+struct fv_adam_s {
+  fv_ctx ctx = nullptr;
+  int64_t n = 0;
+  fv_precision prec = FV_FP32;
+  double beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+  int with_eps = 0;
+  void* m = nullptr;                // [n] (+ eps slot in me)
+  void* v = nullptr;
+  double* me = nullptr;             // [2]: m, v of eps
+  int* t = nullptr;                 // step count (device)
+};
+
+namespace fv {
+
+// Workspace: grows on demand (synchronous cudaMalloc).
+int ws_reserve(fv_ctx ctx, size_t bytes, void** out);
+
+// Timing hooks around each launch (no-ops unless ctx->timing).
+void time_begin(fv_ctx ctx, int kind, cudaEvent_t* a);
+void time_end(fv_ctx ctx, int kind, cudaEvent_t a);
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <class T> struct Real;
+template <> struct Real<double> { using type = double; };
+template <> struct Real<float> { using type = float; };
+template <> struct Real<__nv_bfloat16> { using type = float; };
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Neumaier-compensated accumulator (Kahan-Babuska), FP64.
+struct KSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+// ------------------------------------------------------------------ launchers
+// Each returns FV_OK or an error code and enqueues on ctx->stream.
+struct EvalPlan {
+  MlpShape shape;
+  fv_precision prec;        // network precision
+  int64_t P_mesh = 0;       // quadrature points
+  int n_bd = 0, n_s = 0;
+  int64_t P_tot = 0;        // P_mesh + n_bd + n_s
+  bool want_grad = false;
+};
+
+int launch_mlp_fwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
+                   void* U);
+int launch_contract(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U, void* UB,
+                    double eps, const double* eps_dev, double bx, double by, double rscale, double* partials,
+                    int* n_partials_out, double* R_out = nullptr);
+int contract_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* elems_per_stage, int* stages,
+                  size_t* smem);
+int launch_bc(fv_ctx ctx, fv_bc bc, const EvalPlan& pl, const void* U, void* UB, double* partial2);
+int launch_mlp_bwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
+                   const void* UB, double* gpart, int* n_blocks_out);
+int mlp_bwd_blocks(fv_ctx ctx, const EvalPlan& pl);
+int launch_finalize(fv_ctx ctx, const EvalPlan& pl, const double* cpart, int n_cpart, const double* bcpart,
+                    const double* gpart, int n_gpart, double inv_norm, double tau, double gamma, int n_bd, int n_s,
+                    void* grad, double* out);
+
+// Tensor-core MLP paths (tcgen05).
+int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
+                      const double* Xextra, void* U);
+int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
+                      const double* Xextra, const void* UB, double* gpart, int* n_blocks_out);
+bool tc_supported(const EvalPlan& pl);
+int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl);
+
+}  // namespace fv

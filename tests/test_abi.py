@@ -1,0 +1,57 @@
+"""The C-ABI library: it loads, exports every entry point that
+include/fastvpinn.h declares, and fails cleanly (an error code, not a crash)
+when no GPU is present."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "fastvpinn.h")).read()
+    return re.findall(r"^(?:int|const char\*)\s+(fv_\w+)\s*\(", hdr, re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_12063_b300 import build, _native
+    build.build()
+    return _native.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_2404_12063_b300 import _native
+    assert set(_declared()) == set(_native.SIGNATURES)
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_2404_12063_b300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
+
+
+def test_null_arguments_are_rejected(lib):
+    from paper_2404_12063_b300 import _native as N
+    assert lib.fv_ctx_create(None, 0, None) == N.FV_ERR_ARG
+    assert b"null" in lib.fv_last_error()
+    assert lib.fv_mesh_info(None, None) == N.FV_ERR_ARG
+    assert lib.fv_kernel_name(3) == b"contract"
+
+
+def test_no_gpu_gives_an_error_code(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2404_12063_b300 import _native as N
+    h = C.c_void_p()
+    rc = lib.fv_ctx_create(C.byref(h), 0, None)
+    assert rc in (N.FV_ERR_CUDA, N.FV_ERR_ARG)

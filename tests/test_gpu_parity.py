@@ -1,0 +1,360 @@
+"""GPU vs oracle parity: the CUDA path through the C ABI against the CPU FP64
+oracle on the same seeded inputs.
+
+Tolerances (relative, norm-wise for vectors): 1e-10 for the FP64 path, 1e-5
+for FP32, 2e-2 for BF16 / TF32.  Full-size cases (configs 2-4 at their
+stated sizes, the launch configuration the benchmark times) are compared in
+full against the oracle run with all host cores.
+"""
+import functools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import fv_inputs as fi
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32": 2e-2, "bf16": 2e-2}
+NTH = os.cpu_count() or 1
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12063_b300 import build
+    build.build()
+    from paper_2404_12063_b300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+@functools.lru_cache(maxsize=None)
+def cfg(k):
+    return fi.CONFIGS[k]()
+
+
+def _with(prob, **kw):
+    d = dict(prob.__dict__)
+    d.update(kw)
+    return fi.Problem(**d)
+
+
+def gpu_eval(api, ctx, prob, precision, storage=None, norm="test", intermediates=False):
+    pb = api.problem_from_inputs(ctx, prob, precision, storage, norm)
+    params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+    if intermediates:
+        out, U, UB, R = pb.intermediates(params)
+        torch.cuda.synchronize()
+        return pb, params, out.cpu().numpy(), U.cpu().double().numpy(), UB.cpu().double().numpy(), R.cpu().numpy()
+    out, grad = pb.loss_grad(params)
+    torch.cuda.synchronize()
+    return pb, params, out.cpu().numpy(), grad.cpu().double().numpy()
+
+
+def oracle_eval(prob, params64, norm=0, **kw):
+    return oracle.Bound(prob, norm=norm).loss_grad(params64, n_threads=NTH, **kw)
+
+
+def check_against_oracle(api, ctx, prob, precision, storage=None, norm="test", tol=None):
+    tol = TOL[precision] if tol is None else tol
+    pb, params, out, grad = gpu_eval(api, ctx, prob, precision, storage, norm)
+    p64 = params.cpu().double().numpy()          # the oracle sees the same (rounded) parameters
+    ref = oracle_eval(prob, p64, 0 if norm == "test" else 1)
+    assert rel(out[0], ref["loss"]) < tol, (out[0], ref["loss"])
+    assert rel(out[1], ref["Lv"]) < tol
+    if len(prob.bd_xy):
+        assert rel(out[2], ref["Lb"]) < tol
+    if len(prob.sensor_xy):
+        assert rel(out[3], ref["Ls"]) < tol
+    assert rel(grad, ref["grad"]) < tol, rel(grad, ref["grad"])
+    if prob.eps != 1.0 or prob.b != (0.0, 0.0):
+        assert rel(out[4], ref["dL_deps"]) < tol, (out[4], ref["dL_deps"])
+    return out, grad, ref
+
+
+# ---------------------------------------------------------------- mesh tensors (a1)
+def test_mesh_tensors_match_oracle(api, ctx):
+    prob = _with(cfg(2), b=(0.3, -0.1))
+    mesh = api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, prob.quad_order, prob.test_order, "fp64", True)
+    X = mesh.quad_points()
+    Xo = oracle.quad_points(prob.mesh, prob.quad_order).reshape(-1, 2)
+    assert np.max(np.abs(X - Xo)) < 1e-15
+    G = mesh.g_tensor()
+    Gx, Gy, Gv, F = oracle.Bound(prob).tensors()
+    scale = np.max(np.abs(Gx))
+    assert np.max(np.abs(G[:, 0] - Gx)) < 1e-13 * scale
+    assert np.max(np.abs(G[:, 1] - Gy)) < 1e-13 * scale
+    assert np.max(np.abs(G[:, 2] - Gv)) < 1e-13 * np.max(np.abs(Gv))
+    forcing = api.Forcing(mesh, prob.f(X[:, 0], X[:, 1]))
+    Fg = forcing.matrix()
+    assert np.max(np.abs(Fg - F)) < 1e-12 * np.max(np.abs(F))
+    assert mesh.g_bytes == prob.mesh.n_elements * 3 * prob.test_order ** 2 * prob.quad_order ** 2 * 8
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("bf16", 8e-3)])
+def test_mesh_tensor_storage_rounding(api, ctx, storage, tol):
+    prob = cfg(1)
+    mesh = api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, prob.quad_order, prob.test_order, storage)
+    G = mesh.g_tensor()
+    Gx, Gy, _, _ = oracle.Bound(prob).tensors()
+    assert np.max(np.abs(G[:, 0] - Gx)) < tol * np.max(np.abs(Gx))
+    assert np.max(np.abs(G[:, 1] - Gy)) < tol * np.max(np.abs(Gy))
+
+
+# ---------------------------------------------------------------- config 1 (FP64, tiny)
+def test_config1_fp64_loss_grad(api, ctx):
+    check_against_oracle(api, ctx, cfg(1), "fp64")
+
+
+def test_config1_fp64_intermediates_elementwise(api, ctx):
+    prob = _with(cfg(1), b=(0.2, -0.3), eps=0.7, params=fi.random_bias_params(cfg(1).widths, 1, 1))
+    pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp64", intermediates=True)
+    ref = oracle_eval(prob, prob.params, want_R=True, want_ubar=True, want_upts=True)
+    P = prob.n_points
+    up = ref["upts"].reshape(-1, 3)
+    for c in range(3):
+        assert np.max(np.abs(U[c, :P] - up[:, c])) < 1e-12 * max(1.0, np.max(np.abs(up[:, c])))
+    assert np.max(np.abs(R - ref["R"])) < 1e-11 * np.max(np.abs(ref["R"]))
+    ub = ref["ubar"].reshape(-1, 2)
+    assert np.max(np.abs(UB[1, :P] - ub[:, 0])) < 1e-11 * np.max(np.abs(ub))
+    assert np.max(np.abs(UB[2, :P] - ub[:, 1])) < 1e-11 * np.max(np.abs(ub))
+    assert np.all(UB[0, :P] == 0.0)
+    # boundary points: u and the seed 2 tau (u - g) / N_D
+    ubd, _, _ = oracle.mlp(prob.widths, prob.params, prob.bd_xy)
+    assert np.max(np.abs(U[0, P:] - ubd)) < 1e-12
+    seed = 2 * prob.tau * (ubd - prob.bd_g) / len(prob.bd_g)
+    assert np.max(np.abs(UB[0, P:] - seed)) < 1e-12 * np.max(np.abs(seed))
+
+
+def test_config1_fp32(api, ctx):
+    check_against_oracle(api, ctx, cfg(1), "fp32")
+
+
+# ---------------------------------------------------------------- config 2 (skewed disc)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config2_full(api, ctx, precision):
+    check_against_oracle(api, ctx, cfg(2), precision)
+
+
+def test_config2_fp32_intermediates_elementwise(api, ctx):
+    prob = cfg(2)
+    pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp32", intermediates=True)
+    ref = oracle_eval(prob, params.cpu().double().numpy(), want_R=True, want_ubar=True, want_upts=True)
+    up = ref["upts"].reshape(-1, 3)
+    P = prob.n_points
+    for c in range(3):
+        assert rel(U[c, :P], up[:, c]) < 1e-5
+    assert rel(R, ref["R"]) < 1e-5
+    assert rel(UB[1:, :P].T, ref["ubar"].reshape(-1, 2)) < 1e-5
+
+
+# ---------------------------------------------------------------- config 3 (annulus, 819k points)
+def test_config3_fp32_full(api, ctx):
+    check_against_oracle(api, ctx, cfg(3), "fp32")
+
+
+def test_config3_fp64_full(api, ctx):
+    check_against_oracle(api, ctx, cfg(3), "fp64")
+
+
+# ---------------------------------------------------------------- config 4 (inverse CD2D, 65536 elements)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config4_full(api, ctx, precision):
+    check_against_oracle(api, ctx, cfg(4), precision)
+
+
+def test_config4_gradient_vs_central_differences(api, ctx):
+    """GPU FP64 gradient against central differences of GPU FP64 losses, on a
+    random subset of coordinates plus eps (inverse-problem mesh, 32x32)."""
+    prob = fi.config4_inverse(32)
+    pb = api.problem_from_inputs(ctx, prob, "fp64")
+    params = torch.tensor(prob.params, dtype=torch.float64, device="cuda")
+    out, grad = pb.loss_grad(params)
+    grad = grad.cpu().numpy()
+    dLde = float(out[4])
+    rng = fi.SplitMix64(11, 4)
+    idx = sorted(set(int(rng.uniform() * len(prob.params)) for _ in range(64)))
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(prob.params[i]))
+        vals = []
+        for s in (1, -1):
+            p = params.clone()
+            p[i] += s * h
+            vals.append(float(pb.loss(p)[0]))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - grad[i]) < 1e-6 * max(1.0, abs(grad[i])), (i, fd, grad[i])
+    h = 1e-6
+    vals = []
+    for s in (1, -1):
+        pb.eps = prob.eps + s * h
+        vals.append(float(pb.loss(params)[0]))
+    pb.eps = prob.eps
+    assert abs((vals[0] - vals[1]) / (2 * h) - dLde) < 1e-6 * max(1.0, abs(dLde))
+
+
+# ---------------------------------------------------------------- ragged sizes and edge cases
+@pytest.mark.parametrize("ne,Q,T", [(1, 2, 1), (3, 3, 2), (17, 13, 9), (3, 5, 5), (2, 32, 16), (37, 7, 3)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_sizes(api, ctx, ne, Q, T, precision):
+    base = fi.rect_grid(ne, 1, 0.0, 1.0, 0.0, 0.3)
+    mesh = fi.jitter_nodes(base, ~fi.boundary_nodes_of(base), 0.2, seed=ne)
+    u, f = fi.sinsin(3.0)
+    widths = [2, 7, 5, 1] if ne % 2 else [2, 13, 1]
+    bd = fi.square_boundary_points(3, 0, 1, 0, 0.3)
+    prob = fi.Problem("ragged", mesh, Q, T, widths, fi.random_bias_params(widths, ne, 1), u, f, bd,
+                      u(bd[:, 0], bd[:, 1]), eps=0.9, b=(0.4, 0.2), tau=2.0)
+    check_against_oracle(api, ctx, prob, precision)
+
+
+def test_no_boundary_and_elem_norm(api, ctx):
+    prob = _with(cfg(1), bd_xy=np.zeros((0, 2)), bd_g=np.zeros(0))
+    check_against_oracle(api, ctx, prob, "fp64", norm="elem")
+
+
+def test_bf16_storage_fp32_network(api, ctx):
+    check_against_oracle(api, ctx, cfg(2), "fp32", storage="bf16", tol=TOL["bf16"])
+
+
+def test_large_weights_saturated_tanh(api, ctx):
+    prob = _with(cfg(1), params=fi.glorot_params(cfg(1).widths, 0, 1, gain=3.0))
+    check_against_oracle(api, ctx, prob, "fp64")
+    check_against_oracle(api, ctx, prob, "fp32")
+
+
+def test_degenerate_element_is_rejected(api, ctx):
+    from paper_2404_12063_b300 import FVError, _native as N
+    m = fi.rect_grid(2, 2)
+    cells = m.cells.copy()
+    cells[3] = cells[3][::-1]      # clockwise: negative Jacobian
+    with pytest.raises(FVError) as ei:
+        api.Mesh(ctx, m.vertices, cells, 4, 3, "fp32")
+    assert ei.value.code == N.FV_ERR_DEGENERATE_ELEMENT
+    assert "element 3" in str(ei.value)
+
+
+def test_argument_errors(api, ctx):
+    from paper_2404_12063_b300 import FVError, _native as N
+    prob = cfg(1)
+    with pytest.raises(FVError) as ei:
+        api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells + 100, 5, 5)
+    assert ei.value.code == N.FV_ERR_ARG
+    with pytest.raises(FVError) as ei:
+        api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, 40, 5)
+    assert ei.value.code == N.FV_ERR_UNSUPPORTED
+    pb = api.problem_from_inputs(ctx, prob, "fp32")
+    other = api.problem_from_inputs(ctx, prob, "fp32")
+    pb.forcing = other.forcing
+    with pytest.raises(FVError) as ei:
+        pb.loss_grad(torch.zeros(pb.net.n_params, device="cuda"))
+    assert ei.value.code == N.FV_ERR_ARG
+    mesh32 = api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, 5, 5, "fp32")
+    with pytest.raises(FVError) as ei:
+        api.problem_from_inputs(ctx, prob, "fp64", mesh=mesh32).loss(torch.zeros(pb.net.n_params, device="cuda",
+                                                                                  dtype=torch.float64))
+    assert ei.value.code == N.FV_ERR_UNSUPPORTED
+    with pytest.raises(FVError) as ei:
+        api.Problem(ctx, pb.mesh, pb.forcing if pb.forcing.mesh is pb.mesh else other.forcing, None,
+                    [2, 200, 1]).loss(torch.zeros(801, device="cuda"))
+    assert ei.value.code in (N.FV_ERR_UNSUPPORTED, N.FV_ERR_ARG)
+
+
+def test_deterministic(api, ctx):
+    prob = cfg(2)
+    pb = api.problem_from_inputs(ctx, prob, "fp32")
+    params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+    o1, g1 = pb.loss_grad(params)
+    o1, g1 = o1.clone(), g1.clone()
+    o2, g2 = pb.loss_grad(params)
+    assert torch.equal(o1, o2) and torch.equal(g1, g2)
+
+
+# ---------------------------------------------------------------- bindings, Adam, batches
+def test_autograd_function(api, ctx):
+    prob = cfg(1)
+    pb = api.problem_from_inputs(ctx, prob, "fp64")
+    params = torch.tensor(prob.params, dtype=torch.float64, device="cuda", requires_grad=True)
+    loss = api.FastVPINNLoss.apply(params, pb)
+    (2.0 * loss).backward()
+    _, grad = pb.loss_grad(params.detach())
+    assert torch.allclose(params.grad, 2.0 * grad, rtol=0, atol=0)
+
+
+def test_mlp_eval_matches_oracle(api, ctx):
+    prob = cfg(3)
+    xy = fi.uniform_points(1000, 5, 9)
+    for prec, tol in (("fp64", 1e-13), ("fp32", 1e-5)):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        p = torch.tensor(prob.params, dtype=dt, device="cuda")
+        out = api.mlp_eval(ctx, prob.widths, p, torch.tensor(xy, device="cuda")).cpu().double().numpy()
+        ref = oracle.mlp(prob.widths, p.cpu().double().numpy(), xy)
+        for c in range(3):
+            assert rel(out[c], ref[c]) < tol
+
+
+def test_inverse_step_adam_update(api, ctx):
+    """One fv_inverse_step with lr > 0 equals the oracle gradient pushed through
+    Adam (Kingma & Ba, bias-corrected) on (theta, eps)."""
+    prob = fi.config4_inverse(16)
+    pb = api.problem_from_inputs(ctx, prob, "fp64")
+    params = torch.tensor(prob.params, dtype=torch.float64, device="cuda")
+    eps = torch.tensor([prob.eps], dtype=torch.float64, device="cuda")
+    adam = api.Adam(ctx, pb.net.n_params, "fp64", with_eps=True)
+    lr, b1, b2, ae = 1e-3, 0.9, 0.999, 1e-8
+    m = np.zeros(len(prob.params) + 1)
+    v = np.zeros_like(m)
+    theta = np.concatenate([prob.params, [prob.eps]])
+    for t in range(1, 4):
+        ref = oracle.Bound(_with(prob, params=theta[:-1], eps=theta[-1])).loss_grad(theta[:-1], n_threads=NTH)
+        g = np.concatenate([ref["grad"], [ref["dL_deps"]]])
+        out, _ = pb.inverse_step(params, eps, adam, lr)
+        torch.cuda.synchronize()
+        assert rel(out[0].item(), ref["loss"]) < 1e-10
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        theta = theta - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + ae)
+        assert rel(params.cpu().numpy(), theta[:-1]) < 1e-10
+        assert abs(eps.item() - theta[-1]) < 1e-12
+
+
+def test_batch_equals_individual_calls(api, ctx):
+    probs = fi.config5_batch(6)
+    pbs = [api.problem_from_inputs(ctx, p, "fp32") for p in probs]
+    params = [torch.tensor(p.params, dtype=torch.float32, device="cuda") for p in probs]
+    batch = api.Batch(ctx, pbs, params)
+    outs, grads = batch.run()
+    for pb, p, o, g in zip(pbs, params, outs, grads):
+        o2, g2 = pb.loss_grad(p)
+        assert torch.equal(o[:4], o2[:4]) and torch.equal(g, g2)
+    # and against the oracle for the first instance
+    ref = oracle_eval(probs[0], params[0].cpu().double().numpy())
+    assert rel(outs[0][0].item(), ref["loss"]) < 1e-5
+    assert rel(grads[0].cpu().double().numpy(), ref["grad"]) < 1e-5
+
+
+def test_kernel_timing_records(api, ctx):
+    prob = cfg(1)
+    pb = api.problem_from_inputs(ctx, prob, "fp32")
+    params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+    ctx.reset_kernel_times()
+    ctx.enable_timing(True)
+    pb.loss_grad(params)
+    t = ctx.kernel_times()
+    ctx.enable_timing(False)
+    ctx.reset_kernel_times()
+    for k in ("mlp_fwd", "contract", "mlp_bwd", "finalize", "bc_seed"):
+        assert k in t and t[k][1] == 1 and t[k][0] > 0
