@@ -82,64 +82,81 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t al(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// Fixed-shape tree sum over a block of 256 threads (deterministic).
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
 // Boundary and sensor terms (Sec. 2.2 L_b, Sec. 4.7 L_s) and their seeds.
 template <class R>
-__global__ void bc_kernel(const double* __restrict__ val, int n_bd, int n_s, double tau, double gamma,
-                          const R* __restrict__ U, R* __restrict__ UB, int64_t P_mesh, int64_t P_tot,
-                          double* __restrict__ partial2) {
-  __shared__ double red[256 * 4];
-  KSum lb, ls;
+__global__ void __launch_bounds__(256) bc_kernel(const double* __restrict__ val, int n_bd, int n_s, double tau,
+                                                 double gamma, const R* __restrict__ U, R* __restrict__ UB,
+                                                 int64_t P_mesh, int64_t P_tot, double* __restrict__ partial2) {
+  __shared__ double red[256];
+  R lb = 0, ls = 0;
+  const R cb = (R)(2.0 * tau / (n_bd > 0 ? n_bd : 1)), cs = (R)(2.0 * gamma / (n_s > 0 ? n_s : 1));
   for (int d = threadIdx.x; d < n_bd + n_s; d += blockDim.x) {
     const int64_t gp = P_mesh + d;
-    const double diff = (double)U[gp] - val[d];
-    double seed;
-    if (d < n_bd) { lb.add(diff * diff); seed = 2.0 * tau * diff / n_bd; }
-    else { ls.add(diff * diff); seed = 2.0 * gamma * diff / n_s; }
+    const R diff = U[gp] - (R)val[d];
+    R seed;
+    if (d < n_bd) { lb += diff * diff; seed = cb * diff; }
+    else { ls += diff * diff; seed = cs * diff; }
     if (UB) {
-      UB[gp] = (R)seed;
+      UB[gp] = seed;
       UB[P_tot + gp] = (R)0;
       UB[2 * P_tot + gp] = (R)0;
     }
   }
-  red[threadIdx.x * 4 + 0] = lb.s; red[threadIdx.x * 4 + 1] = lb.c;
-  red[threadIdx.x * 4 + 2] = ls.s; red[threadIdx.x * 4 + 3] = ls.c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    KSum a, b;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      a.add(red[t * 4]); a.add(red[t * 4 + 1]);
-      b.add(red[t * 4 + 2]); b.add(red[t * 4 + 3]);
-    }
-    partial2[0] = a.value();
-    partial2[1] = b.value();
-  }
+  const double a = block_sum256((double)lb, red);
+  const double b = block_sum256((double)ls, red);
+  if (threadIdx.x == 0) { partial2[0] = a; partial2[1] = b; }
 }
 
-// Deterministic final sums: gradient over per-CTA partials (fixed order) and
-// the loss scalars.  out = (L, Lv, Lb, Ls, dL/deps).
+// Deterministic final sums: the gradient over per-CTA partials and the loss
+// scalars, both as fixed-shape trees.  out = (L, Lv, Lb, Ls, dL/deps).
+// Gradient: 8 threads per parameter, each summing a strided subset of the
+// partials, then a 3-level shuffle tree.
 template <class R>
-__global__ void finalize_kernel(const double* __restrict__ cpart, int n_cpart, const double* __restrict__ bcpart,
-                                const double* __restrict__ gpart, int n_gpart, int n_params, double inv_norm,
-                                double tau, double gamma, int n_bd, int n_s, R* __restrict__ grad,
-                                double* __restrict__ out) {
+__global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ cpart, int n_cpart,
+                                                       const double* __restrict__ bcpart,
+                                                       const double* __restrict__ gpart, int n_gpart, int n_params,
+                                                       double inv_norm, double tau, double gamma, int n_bd, int n_s,
+                                                       R* __restrict__ grad, double* __restrict__ out) {
+  __shared__ double red[256];
   if (grad) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_params; i += gridDim.x * blockDim.x) {
-      double s = 0.0;
-      for (int b = 0; b < n_gpart; ++b) s += gpart[(size_t)b * n_params + i];
-      grad[i] = (R)s;
-    }
+    const int sub = threadIdx.x & 7;
+    const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+    double s = 0.0;
+    if (i < n_params)
+      for (int b = sub; b < n_gpart; b += 8) s += gpart[(size_t)b * n_params + i];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (i < n_params && sub == 0) grad[i] = (R)s;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    KSum l, d;
-    for (int b = 0; b < n_cpart; ++b) { l.add(cpart[2 * b]); d.add(cpart[2 * b + 1]); }
-    const double Lv = inv_norm * l.value();
-    const double Lb = n_bd ? bcpart[0] / n_bd : 0.0;
-    const double Ls = n_s ? bcpart[1] / n_s : 0.0;
-    out[0] = Lv + tau * Lb + gamma * Ls;
-    out[1] = Lv;
-    out[2] = Lb;
-    out[3] = Ls;
-    out[4] = d.value();
+  if (blockIdx.x == 0) {
+    double l = 0.0, d = 0.0;
+    for (int b = threadIdx.x; b < n_cpart; b += blockDim.x) { l += cpart[2 * b]; d += cpart[2 * b + 1]; }
+    l = block_sum256(l, red);
+    d = block_sum256(d, red);
+    if (threadIdx.x == 0) {
+      const double Lv = inv_norm * l;
+      const double Lb = n_bd ? bcpart[0] / n_bd : 0.0;
+      const double Ls = n_s ? bcpart[1] / n_s : 0.0;
+      out[0] = Lv + tau * Lb + gamma * Ls;
+      out[1] = Lv;
+      out[2] = Lb;
+      out[3] = Ls;
+      out[4] = d;
+    }
   }
 }
 
@@ -279,7 +296,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   cudaEvent_t ta;
   time_begin(ctx, K_FINALIZE, &ta);
   const double tau = bc ? bc->tau : 0.0, gamma = bc ? bc->gamma : 0.0;
-  const int fgrid = want_grad ? std::max(1, std::min(ctx->n_sm, (sh.n_params + 255) / 256)) : 1;
+  const int fgrid = want_grad ? std::max(1, (sh.n_params + 31) / 32) : 1;
   if (pl.prec == FV_FP64)
     finalize_kernel<double><<<fgrid, 256, 0, ctx->stream>>>(cpart, ncp, bcpart, gpart, ngp, sh.n_params, inv_norm, tau,
                                                             gamma, pl.n_bd, pl.n_s, (double*)grad, out);

@@ -98,6 +98,7 @@ struct fv_mesh_s {
 struct fv_forcing_s {
   fv_mesh mesh = nullptr;
   double* F = nullptr;              // [n_e][Nt]
+  float* F32 = nullptr;             // FP32 copy for the FP32 / tensor-core paths
 };
 
 struct fv_bc_s {

@@ -170,6 +170,11 @@ __global__ void forcing_kernel(const double* __restrict__ verts, const int* __re
   }
 }
 
+__global__ void to_float_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 template <class Gt>
 __global__ void g_to_double_kernel(const Gt* __restrict__ G, int64_t stride, int n_e, int64_t per_elem,
                                    double* __restrict__ out) {
@@ -332,8 +337,9 @@ extern "C" int fv_assemble_forcing(fv_mesh m, const double* f, fv_forcing* out) 
   fv_forcing fo = new fv_forcing_s();
   fo->mesh = m;
   cudaError_t e;
-  if ((e = cudaMalloc(&fo->F, sizeof(double) * m->n_e * m->Nt)) || (e = cudaMalloc(&fd, sizeof(double) * m->P))) {
-    cudaFree(fo->F); cudaFree(fd); delete fo;
+  if ((e = cudaMalloc(&fo->F, sizeof(double) * m->n_e * m->Nt)) ||
+      (e = cudaMalloc(&fo->F32, sizeof(float) * m->n_e * m->Nt)) || (e = cudaMalloc(&fd, sizeof(double) * m->P))) {
+    cudaFree(fo->F); cudaFree(fo->F32); cudaFree(fd); delete fo;
     set_error("fv_assemble_forcing: cudaMalloc failed (%s)", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;
   }
@@ -344,13 +350,14 @@ extern "C" int fv_assemble_forcing(fv_mesh m, const double* f, fv_forcing* out) 
     time_begin(ctx, K_FORCING, &ta);
     forcing_kernel<<<(int)std::min<int64_t>(m->n_e, ctx->n_sm * 8), 128, 0, st>>>(m->verts, m->cells, m->n_e, m->Q,
                                                                                   m->T, m->tables, fd, fo->F);
+    to_float_kernel<<<ctx->n_sm, 256, 0, st>>>(fo->F, fo->F32, (int64_t)m->n_e * m->Nt);
     time_end(ctx, K_FORCING, ta);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(fd);
   if (e != cudaSuccess) {
-    cudaFree(fo->F); delete fo;
+    cudaFree(fo->F); cudaFree(fo->F32); delete fo;
     set_error("fv_assemble_forcing: %s", cudaGetErrorString(e));
     return FV_ERR_CUDA;
   }
@@ -371,6 +378,7 @@ extern "C" int fv_forcing_destroy(fv_forcing fo) {
   clear_error();
   if (!fo) return FV_OK;
   cudaFree(fo->F);
+  cudaFree(fo->F32);
   delete fo;
   return FV_OK;
 }

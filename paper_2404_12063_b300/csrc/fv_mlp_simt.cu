@@ -19,8 +19,9 @@
 // micro-tile fall in distinct bank groups).  Each layer is a small GEMM done
 // as 4x4 register micro-tiles.  The reverse kernel recomputes the forward for
 // its tile, keeps every hidden layer's (t, t'_x, t'_y) on chip, and
-// accumulates the weight gradient of all its tiles in an FP64 shared-memory
-// buffer that it writes out once (deterministic per-CTA partials).
+// accumulates the weight gradient of all its tiles in a shared-memory buffer
+// (FP64, or compensated FP32 pairs on the FP32 path) that it writes out once
+// (deterministic per-CTA partials).
 #include <algorithm>
 
 #include "fv_internal.cuh"
@@ -108,6 +109,30 @@ __device__ __forceinline__ void st4(double* p, const double v[4]) {
 }
 __device__ __forceinline__ float tanh_r(float v) { return tanhf(v); }
 __device__ __forceinline__ double tanh_r(double v) { return tanh(v); }
+
+// Per-CTA weight-gradient accumulator in shared memory: FP64 on the FP64
+// path; on the FP32 path a compensated (Kahan) FP32 pair per entry, which
+// keeps FP64 arithmetic (slow on this part) out of the tile loop.
+template <class R> struct GradAcc;
+template <> struct GradAcc<double> {
+  double* a;
+  __device__ __forceinline__ void zero(int i) { a[i] = 0.0; }
+  __device__ __forceinline__ void add(int i, double v) { a[i] += v; }
+  __device__ __forceinline__ double get(int i) const { return a[i]; }
+};
+template <> struct GradAcc<float> {
+  float2* a;   // (sum, compensation)
+  __device__ __forceinline__ void zero(int i) { a[i] = make_float2(0.f, 0.f); }
+  __device__ __forceinline__ void add(int i, float v) {
+    float2 t = a[i];
+    const float y = v - t.y;
+    const float u = t.x + y;
+    t.y = (u - t.x) - y;
+    t.x = u;
+    a[i] = t;
+  }
+  __device__ __forceinline__ double get(int i) const { return (double)a[i].x - (double)a[i].y; }
+};
 
 // Load the padded weights into shared memory (zero padding).
 template <class R>
@@ -268,7 +293,7 @@ __device__ void bwd_elementwise(const R* __restrict__ S, const R* __restrict__ T
 // interleaved rows (o = og + n_og*oo, k = kg + n_kg*kk).
 template <class R>
 __device__ void wgrad_layer(const R* __restrict__ Zb, const R* __restrict__ H, int out, int in, int rows_o,
-                            int rows_k, int TP, int TPS, int plane, double* gW) {
+                            int rows_k, int TP, int TPS, int plane, GradAcc<R> G, int off) {
   const int n_og = rows_o >> 2, n_kg = rows_k >> 2;
   for (int mt = threadIdx.x; mt < n_og * n_kg; mt += blockDim.x) {
     const int kg = mt % n_kg, og = mt / n_kg;
@@ -299,7 +324,7 @@ __device__ void wgrad_layer(const R* __restrict__ Zb, const R* __restrict__ H, i
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const int o = og + oo * n_og, k = kg + kk * n_kg;
-        if (o < out && k < in) gW[o * in + k] += (double)acc[oo][kk];
+        if (o < out && k < in) G.add(off + o * in + k, acc[oo][kk]);
       }
   }
 }
@@ -307,21 +332,21 @@ __device__ void wgrad_layer(const R* __restrict__ Zb, const R* __restrict__ H, i
 // Layer-0 weight gradient: inputs (x, y), tangents (1,0) and (0,1).
 template <class R>
 __device__ void wgrad_layer0(const R* __restrict__ Zb, const R* __restrict__ sX, int out, int TP, int TPS,
-                             int plane, double* gW) {
+                             int plane, GradAcc<R> G, int off) {
   for (int idx = threadIdx.x; idx < 2 * out; idx += blockDim.x) {
     const int o = idx >> 1, c = idx & 1;
     R acc = 0;
     for (int p = 0; p < TP; ++p) acc += Zb[o * TPS + p] * sX[c * TPS + p] + Zb[(1 + c) * plane + o * TPS + p];
-    gW[o * 2 + c] += (double)acc;
+    G.add(off + o * 2 + c, acc);
   }
 }
 
 template <class R>
-__device__ void bgrad(const R* __restrict__ Zb, int out, int TP, int TPS, double* gb) {
+__device__ void bgrad(const R* __restrict__ Zb, int out, int TP, int TPS, GradAcc<R> G, int off) {
   for (int o = threadIdx.x; o < out; o += blockDim.x) {
     R acc = 0;
     for (int p = 0; p < TP; ++p) acc += Zb[o * TPS + p];
-    gb[o] += (double)acc;
+    G.add(off + o, acc);
   }
 }
 
@@ -370,14 +395,15 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
   const WLayout& wl = a.wl;
   const int L = sh.L, TP = a.TP, TPS = a.TPS;
   const int plane = a.DP * TPS;
-  double* gAcc = reinterpret_cast<double*>(smem);                 // [n_params] (rounded to even)
-  R* sW = reinterpret_cast<R*>(gAcc + ((sh.n_params + 1) & ~1));
+  GradAcc<R> G;
+  G.a = reinterpret_cast<decltype(G.a)>(smem);                     // [n_params] 8-byte entries (rounded to even)
+  R* sW = reinterpret_cast<R*>(smem + 8 * (size_t)((sh.n_params + 1) & ~1));
   R* S = sW + wl.total;                                           // [L-1][3][DP][TPS]
   R* Zb = S + (size_t)(L - 1) * 3 * plane;
   R* Tb = Zb + 3 * plane;
   R* sX = Tb + 3 * plane;                                         // [2][TPS]
   R* sSeed = sX + 2 * TPS;                                        // [3][TPS]
-  for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) gAcc[i] = 0.0;
+  for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) G.zero(i);
   load_weights<R>(sh, wl, reinterpret_cast<const R*>(a.params), sW);
   const R* UB = reinterpret_cast<const R*>(a.UB);
   const int64_t n_tiles = (a.P_tot + TP - 1) / TP;
@@ -406,18 +432,18 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
       const int in = sh.w[L - 1];
       const R* H = S + (size_t)(L - 2) * 3 * plane;
       const R* Wl = sW + wl.woff[L - 1];
-      double* gW = gAcc + sh.off[L - 1];
+      const int goff = sh.off[L - 1];
       for (int k = threadIdx.x; k < in; k += blockDim.x) {
         R acc = 0;
         for (int p = 0; p < TP; ++p)
           acc += sSeed[p] * H[k * TPS + p] + sSeed[TPS + p] * H[plane + k * TPS + p] +
                  sSeed[2 * TPS + p] * H[2 * plane + k * TPS + p];
-        gW[k] += (double)acc;
+        G.add(goff + k, acc);
       }
       if (threadIdx.x == 0) {
         R acc = 0;
         for (int p = 0; p < TP; ++p) acc += sSeed[p];
-        gW[in] += (double)acc;
+        G.add(goff + in, acc);
       }
       const int rows = wl.rows[L - 2];
       for (int idx = threadIdx.x; idx < rows * TP; idx += blockDim.x) {
@@ -435,19 +461,19 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
       const R* Si = S + (size_t)i * 3 * plane;
       bwd_elementwise<R>(Si, Tb, Zb, wl.rows[i], TP, TPS, plane);
       __syncthreads();
-      double* gW = gAcc + sh.off[i];
+      const int goff = sh.off[i];
       if (i >= 1)
-        wgrad_layer<R>(Zb, S + (size_t)(i - 1) * 3 * plane, out, in, wl.rows[i], wl.ld[i], TP, TPS, plane, gW);
+        wgrad_layer<R>(Zb, S + (size_t)(i - 1) * 3 * plane, out, in, wl.rows[i], wl.ld[i], TP, TPS, plane, G, goff);
       else
-        wgrad_layer0<R>(Zb, sX, out, TP, TPS, plane, gW);
-      bgrad<R>(Zb, out, TP, TPS, gW + out * in);
+        wgrad_layer0<R>(Zb, sX, out, TP, TPS, plane, G, goff);
+      bgrad<R>(Zb, out, TP, TPS, G, goff + out * in);
       if (i >= 1) tbar_layer<R>(sW + wl.woff[i], wl.ld[i], out, wl.ld[i], Zb, Tb, TP, TPS, plane);
       __syncthreads();
     }
   }
   __syncthreads();
   double* dst = a.gpart + (size_t)blockIdx.x * sh.n_params;
-  for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) dst[i] = gAcc[i];
+  for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) dst[i] = G.get(i);
 }
 
 size_t fwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rsz) {
