@@ -241,7 +241,7 @@ def main():
     if args.precision != "auto":
         variants = [args.precision]
     else:
-        for p in ("bf16", "tf32"):
+        for p in ("bf16", "fp16"):
             try:
                 pb_try = api.problem_from_inputs(ctx, fi.config1_tiny(), p)
                 pb_try.loss_grad(torch.tensor(fi.config1_tiny().params, dtype=torch.float32, device="cuda"))
@@ -267,7 +267,7 @@ def main():
     P_tot = prob.n_points + len(prob.bd_xy)
     results = {}
     for v in variants:
-        storage = "bf16" if v == "bf16" else "fp32"
+        storage = "bf16" if v in ("bf16", "fp16") else "fp32"
         pb = api.problem_from_inputs(ctx, prob, v, storage=storage, mesh=meshes[storage])
         params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
         grad = torch.empty_like(params)
@@ -322,7 +322,7 @@ def main():
     del ref64
 
     # headline: the fastest variant within its stated tolerance
-    tol = {"fp32": 1e-5, "tf32": 2e-2, "bf16": 2e-2, "fp64": 1e-10}
+    tol = {"fp32": 1e-5, "tf32": 2e-2, "bf16": 2e-2, "fp16": 2e-2, "fp64": 1e-10}
     ok = [v for v in results if results[v]["err_loss"] < tol[v] and results[v]["err_grad"] < tol[v]]
     head = min(ok or list(results), key=lambda v: results[v]["ms"])
     r = results[head]
@@ -333,9 +333,10 @@ def main():
         t = r["kt"].get(name)
         return (t[0] / t[1]) if t else None
 
-    mesh = meshes["bf16" if head == "bf16" else "fp32"]
-    cbytes, gbytes = contract_bytes(mesh, 2 if head == "bf16" else 4)
-    tc = head in ("bf16", "tf32")
+    g16 = head in ("bf16", "fp16")
+    mesh = meshes["bf16" if g16 else "fp32"]
+    cbytes, gbytes = contract_bytes(mesh, 2 if g16 else 4)
+    tc = head in ("bf16", "tf32", "fp16")
     kinds = {k: v for k, v in r["kt"].items()}
     dom = max(kinds, key=lambda k: kinds[k][0]) if kinds else None
     c_ms = kavg("contract")
@@ -350,10 +351,10 @@ def main():
         fl = (bwd_fl if "bwd" in dom else fwd_fl) * P_tot
         ach = fl / (kavg(dom) * 1e-3) / 1e12
         if tc:
-            pk = bf16_sus if head == "bf16" else bf16_sus / 2
+            pk = bf16_sus if head in ("bf16", "fp16") else bf16_sus / 2
             roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": None, "kernel": dom, "peak_kind": peak_kind + " sustained bf16" +
-                    ("" if head == "bf16" else " x 1/2 (tf32 nominal ratio)")}
+                    "traffic": None, "kernel": dom, "peak_kind": peak_kind + " sustained bf16 (fp16 dense rate "
+                    "is the same)"}
         else:
             pk = 148 * 128 * 2 * sm_max * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
@@ -383,11 +384,11 @@ def main():
         "metric": METRIC, "value": evals, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32/f32-accum", "bf16": "bf16/f32-accum",
-                                       "fp64": "f64"}[head],
+                                       "fp16": "f16/f32-accum", "fp64": "f64"}[head],
         "data": "synthetic",
         "config": {"workload": prob.name, "elements": prob.mesh.n_elements, "Q": prob.quad_order,
                    "T": prob.test_order, "quad_points": prob.n_points, "boundary_points": len(prob.bd_xy),
-                   "mlp": "2-50x4-1", "variant": head, "g_storage": "bf16" if head == "bf16" else "fp32",
+                   "mlp": "2-50x4-1", "variant": head, "g_storage": "bf16" if g16 else "fp32",
                    "l2": "inputs larger than L2 (G = %.0f MB)" % (gbytes / 1e6), "parallelism": "replicas"},
         "quad_pts_per_s": world * prob.n_points * 1e3 / r["ms"],
         "variants": variants_out,

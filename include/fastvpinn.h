@@ -58,7 +58,7 @@ enum {
   FV_ERR_TIMEOUT = 6              /* a bounded device-side wait gave up */
 };
 
-typedef enum { FV_FP64 = 0, FV_FP32 = 1, FV_TF32 = 2, FV_BF16 = 3 } fv_precision;
+typedef enum { FV_FP64 = 0, FV_FP32 = 1, FV_TF32 = 2, FV_BF16 = 3, FV_FP16 = 4 } fv_precision;
 typedef enum { FV_NORM_TEST = 0, FV_NORM_ELEM = 1 } fv_norm;
 
 typedef struct fv_ctx_s* fv_ctx;
@@ -79,7 +79,9 @@ typedef struct {
 
 /* Per-evaluation options. */
 typedef struct {
-  fv_precision mlp_precision; /* FV_FP64, FV_FP32 (CUDA-core FMA), FV_TF32 / FV_BF16 (tensor cores, FP32 accumulate) */
+  fv_precision mlp_precision; /* FV_FP64, FV_FP32: CUDA-core FMA.  FV_BF16, FV_FP16: tcgen05 tensor cores,
+                                 16-bit operands, FP32 accumulation (FP16 scales the reverse-sweep
+                                 adjoints by a power of two).  FV_TF32 returns FV_ERR_UNSUPPORTED. */
   double eps;                 /* diffusion coefficient (Eq. CD2D_strong); used when eps_dev is NULL */
   const double* eps_dev;      /* optional device scalar read by the kernels instead of eps */
   double bx, by;              /* convection velocity b */

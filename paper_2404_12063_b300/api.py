@@ -15,7 +15,7 @@ import torch
 
 from . import _native as N
 
-PRECISIONS = {"fp64": N.FV_FP64, "fp32": N.FV_FP32, "tf32": N.FV_TF32, "bf16": N.FV_BF16}
+PRECISIONS = {"fp64": N.FV_FP64, "fp32": N.FV_FP32, "tf32": N.FV_TF32, "bf16": N.FV_BF16, "fp16": N.FV_FP16}
 NORMS = {"test": N.FV_NORM_TEST, "elem": N.FV_NORM_ELEM}
 
 

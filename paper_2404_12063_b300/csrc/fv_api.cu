@@ -160,6 +160,18 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict_
   }
 }
 
+// max |seed| over all points (the FP16 reverse sweep scales its adjoints by
+// a power of two derived from it); non-negative floats order like their bits.
+__global__ void __launch_bounds__(256) seed_absmax_kernel(const float* __restrict__ UB, int64_t n,
+                                                          float* __restrict__ out) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(UB[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+}
+
 template <class R>
 __global__ void adam_kernel(R* __restrict__ p, const R* __restrict__ g, int64_t n, R* __restrict__ m,
                             R* __restrict__ v, double* eps_p, const double* dLde, double* me, int with_eps, int* t,
@@ -196,7 +208,7 @@ int check_eval(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_
     return FV_ERR_UNSUPPORTED;
   }
   const fv_precision p = opts->mlp_precision;
-  if (p != FV_FP64 && p != FV_FP32 && p != FV_TF32 && p != FV_BF16) {
+  if (p != FV_FP64 && p != FV_FP32 && p != FV_TF32 && p != FV_BF16 && p != FV_FP16) {
     set_error("evaluation: unknown precision");
     return FV_ERR_UNSUPPORTED;
   }
@@ -212,7 +224,7 @@ int check_eval(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_
 }
 
 struct WsLayout {
-  size_t U, UB, cpart, bcpart, gpart, total;
+  size_t U, UB, cpart, bcpart, gpart, smax, total;
 };
 
 // The core evaluation shared by fv_loss, fv_loss_grad and fv_inverse_step.
@@ -230,7 +242,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   pl.n_s = bc ? bc->n_s : 0;
   pl.P_tot = pl.P_mesh + pl.n_bd + pl.n_s;
   pl.want_grad = want_grad;
-  const bool tc = pl.prec == FV_TF32 || pl.prec == FV_BF16;
+  const bool tc = pl.prec == FV_TF32 || pl.prec == FV_BF16 || pl.prec == FV_FP16;
   if (tc && !tc_supported(pl)) {
     set_error("tensor-core path does not support this network shape");
     return FV_ERR_UNSUPPORTED;
@@ -251,6 +263,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   w.cpart = o; o += al(2 * (size_t)cgrid * 8);
   w.bcpart = o; o += al(2 * 8);
   w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
+  w.smax = o; o += al(16);
   w.total = o;
   void* base;
   rc = ws_reserve(ctx, w.total, &base);
@@ -261,6 +274,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   double* cpart = reinterpret_cast<double*>(b + w.cpart);
   double* bcpart = reinterpret_cast<double*>(b + w.bcpart);
   double* gpart = reinterpret_cast<double*>(b + w.gpart);
+  float* smax = reinterpret_cast<float*>(b + w.smax);
   const double* Xe = bc ? bc->xy : nullptr;
 
   rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U) : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
@@ -288,8 +302,16 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   if (UB_copy && UB)
     FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, 3 * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
   int ngp = 0;
+  if (want_grad && pl.prec == FV_FP16) {
+    cudaEvent_t ts;
+    time_begin(ctx, K_SEED_SCALE, &ts);
+    FV_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(float), ctx->stream));
+    seed_absmax_kernel<<<ctx->n_sm * 2, 256, 0, ctx->stream>>>((const float*)UB, 3 * pl.P_tot, smax);
+    time_end(ctx, K_SEED_SCALE, ts);
+    FV_CUDA_TRY(cudaGetLastError());
+  }
   if (want_grad) {
-    rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp)
+    rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp, smax)
             : launch_mlp_bwd(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp);
     if (rc) return rc;
   }
@@ -405,7 +427,7 @@ extern "C" int fv_ctx_reset_kernel_times(fv_ctx ctx) {
 
 extern "C" const char* fv_kernel_name(int kind) {
   static const char* names[K_NUM_KINDS] = {"g_build", "forcing", "mlp_fwd", "contract", "bc_seed", "mlp_bwd",
-                                           "finalize", "adam", "mlp_fwd_tc", "mlp_bwd_tc", "batch"};
+                                           "finalize", "adam", "mlp_fwd_tc", "mlp_bwd_tc", "batch", "seed_scale"};
   return (kind >= 0 && kind < K_NUM_KINDS) ? names[kind] : "";
 }
 
@@ -462,7 +484,8 @@ extern "C" int fv_adam_create(fv_ctx ctx, int64_t n, fv_precision prec, double b
                               fv_adam* out) {
   clear_error();
   FV_CHECK_ARG(ctx && out && n > 0, "fv_adam_create: bad argument");
-  FV_CHECK_ARG(prec == FV_FP64 || prec == FV_FP32 || prec == FV_TF32 || prec == FV_BF16, "fv_adam_create: precision");
+  FV_CHECK_ARG(prec == FV_FP64 || prec == FV_FP32 || prec == FV_TF32 || prec == FV_BF16 || prec == FV_FP16,
+               "fv_adam_create: precision");
   FV_CUDA_TRY(cudaSetDevice(ctx->device));
   fv_adam a = new fv_adam_s();
   a->ctx = ctx; a->n = n; a->prec = prec == FV_FP64 ? FV_FP64 : FV_FP32;

@@ -43,7 +43,7 @@ constexpr int kMaxT = 16;
 // Kernel kinds for the optional per-kernel event timing.
 enum KernelKind {
   K_G_BUILD = 0, K_FORCING, K_MLP_FWD, K_CONTRACT, K_BC, K_MLP_BWD, K_FINALIZE, K_ADAM,
-  K_MLP_FWD_TC, K_MLP_BWD_TC, K_BATCH, K_NUM_KINDS
+  K_MLP_FWD_TC, K_MLP_BWD_TC, K_BATCH, K_SEED_SCALE, K_NUM_KINDS
 };
 
 // Network shape passed to kernels by value.
@@ -190,7 +190,8 @@ int launch_finalize(fv_ctx ctx, const EvalPlan& pl, const double* cpart, int n_c
 int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
                       const double* Xextra, void* U);
 int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
-                      const double* Xextra, const void* UB, double* gpart, int* n_blocks_out);
+                      const double* Xextra, const void* UB, double* gpart, int* n_blocks_out,
+                      const float* seed_absmax);
 bool tc_supported(const EvalPlan& pl);
 int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl);
 

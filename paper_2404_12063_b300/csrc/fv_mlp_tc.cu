@@ -1,24 +1,891 @@
-// Tensor-core (tcgen05) MLP forward/reverse for the FV_TF32 / FV_BF16 paths.
+// tanh-MLP forward with tangents and its reverse sweep on the 5th-generation
+// tensor cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+// Same mathematics as the CUDA-core kernels (Sec. 2.2 Eq. NN; forward-mode
+// tangents d/dx, d/dy; reverse sweep through the tanh rule):
+//
+//   forward  map i:  Z_s = H_{i-1,s} W_i^T (+ b_i on the value stream)   s in {value, d/dx, d/dy}
+//            t = tanh z, t'_s = (1 - t^2) z'_s
+//   reverse  map i:  Zbar from Tbar and (t, t'_x, t'_y) (tanh rule),
+//            Wbar_i += sum_s Zbar_s^T H_{i-1,s}     (bias gradient from a ones column)
+//            Tbar_{i-1,s} = Zbar_s W_i
+//
+// A CTA of 256 threads handles tiles of 128 points: point p is row p of every
+// GEMM tile and lane p of tensor memory; warps w and w+4 share TMEM lane
+// quarter w and split the tile's columns between them.  All three
+// GEMMs read the same shared-memory tiles: activations are stored once in the
+// no-swizzle core-matrix layout (8 rows x 16 bytes) and addressed as K-major
+// operands (forward, Tbar) or as MN-major operands (weight gradient, and W_i
+// for Tbar).  Layer 0 (two inputs) and the output layer (one output) run on
+// CUDA cores.  The bias of each hidden map rides in an extra weight column
+// that multiplies a constant-1 activation column, so the tensor core adds it
+// and the weight-gradient GEMM returns the bias gradient in that column.
+#include <algorithm>
+
 #include "fv_internal.cuh"
 
 namespace fv {
+namespace {
 
-bool tc_supported(const EvalPlan& pl) { (void)pl; return false; }
+constexpr int kTcThreads = 256;
+constexpr int kTile = 128;
+constexpr uint64_t kTcWaitNs = 2000000000ull;
 
-int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl) { (void)ctx; (void)pl; return -FV_ERR_UNSUPPORTED; }
+inline int ru16(int v) { return (v + 15) & ~15; }
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (gtimer() - t0 > kTcWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle: start, LBO (K-direction core
+// matrix stride), SBO (M/N-direction 8-row group stride), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: D F32, A/B format fmt (0 F16, 1 BF16), majors, N, M.
+__device__ __forceinline__ uint32_t idesc_f16(uint32_t fmt, int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 16-bit operand formats for kind::f16: BF16 (8-bit significand, FP32 range)
+// or FP16 (11-bit significand; the reverse sweep scales its adjoints by a
+// power of two to stay inside FP16's range).
+struct OpBF16 {
+  static constexpr uint32_t fmt = 1;
+  __device__ static __forceinline__ uint32_t pack(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+  }
+  __device__ static __forceinline__ float lo(uint32_t u) { return __uint_as_float(u << 16); }
+  __device__ static __forceinline__ float hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+};
+struct OpF16 {
+  static constexpr uint32_t fmt = 0;
+  __device__ static __forceinline__ uint32_t pack(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+  }
+  __device__ static __forceinline__ float lo(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu))); }
+  __device__ static __forceinline__ float hi(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)(u >> 16))); }
+};
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Activation tile layout (one stream): row p, column k of a [128 x Kb] BF16
+// tile: (p/8)*Kb*16 + (k/8)*128 + (p%8)*16 + (k%8)*2 bytes.  A stream spans
+// 256*Kb bytes.
+__device__ __forceinline__ uint32_t row_off(int p, int Kb) { return (p >> 3) * (Kb * 16) + (p & 7) * 16; }
+
+__device__ __forceinline__ void st16(uint8_t* stream, int Kb, int p, int c0, const uint32_t pk[8]) {
+  uint8_t* b = stream + row_off(p, Kb) + (c0 >> 3) * 128;
+  *reinterpret_cast<uint4*>(b) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  *reinterpret_cast<uint4*>(b + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+template <class OP>
+__device__ __forceinline__ void ld16(const uint8_t* stream, int Kb, int p, int c0, float v[16]) {
+  const uint8_t* b = stream + row_off(p, Kb) + (c0 >> 3) * 128;
+  const uint4 x = *reinterpret_cast<const uint4*>(b);
+  const uint4 y = *reinterpret_cast<const uint4*>(b + 128);
+  const uint32_t u[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { v[2 * i] = OP::lo(u[i]); v[2 * i + 1] = OP::hi(u[i]); }
+}
+
+// ------------------------------------------------------------------ plan
+struct TcPlan {
+  int L;
+  int w[kMaxLayers + 1];
+  int off[kMaxLayers];
+  int n_params;
+  int WP[kMaxLayers];       // padded width of the output of hidden map i: ru16(w[i+1] + 1)
+  int HP;                   // max WP (32 or 64)
+  int o_w[kMaxLayers];      // byte offset of BF16 W_i (maps 1..L-2): [WP_i rows][WP_{i-1} cols], bias in col w_i
+  int o_small;              // FP32: w0x[HP], w0y[HP], b0[HP], wL[HP], bL
+  int o_buf[2];             // activation tiles (3 streams x 128 x HP BF16)
+  int o_z;                  // adjoint tile (reverse kernel)
+  int o_x;                  // layer-0 input tile (reverse kernel): 3 streams x 128 x 16
+  int o_red;                // FP32 scratch [128][4] (output-layer partial sums)
+  int o_bar;                // mbarrier (8 B) + TMEM base (4 B) + flags (4 B)
+  int smem;
+  int tmem_cols;
+  int c_wbar[kMaxLayers];   // TMEM column of the weight-gradient accumulator of map i (reverse)
+};
+
+struct TcArgs {
+  TcPlan pl;
+  const float* params;
+  const double* Xm;
+  int64_t P_mesh;
+  const double* Xe;
+  int64_t P_tot;
+  float* U;                 // [3][P_tot] (forward)
+  const float* UB;          // [3][P_tot] seeds (reverse)
+  double* gpart;            // [grid][n_params] (reverse)
+  const float* seed_absmax; // device max |seed| (FP16 reverse sweep) or null
+  int* err;
+};
+
+// Power-of-two scale 2^-e with max|seed| <= 2^e, so scaled seeds lie in [-1, 1]
+// (exact to apply and to undo).
+__device__ __forceinline__ float seed_scale(const float* absmax) {
+  if (!absmax) return 1.f;
+  const float m = *absmax;
+  if (!(m > 0.f) || !isfinite(m)) return 1.f;
+  int e;
+  frexpf(m, &e);               // m = f 2^e, f in [0.5, 1)
+  e = max(-100, min(100, e));
+  return __int_as_float((127 - e) << 23);
+}
+
+// W_i (maps 1..L-2) as BF16 K-major core-matrix tiles, bias folded in column w_i;
+// layer-0 and output-layer weights in FP32.
+template <class OP>
+__device__ void tc_load_weights(const TcPlan& pl, const float* __restrict__ P, uint8_t* sm) {
+  const int L = pl.L;
+  for (int i = 1; i <= L - 2; ++i) {
+    const int in = pl.w[i], out = pl.w[i + 1], Kb = pl.WP[i - 1], Nr = pl.WP[i];
+    const float* W = P + pl.off[i];
+    uint16_t* dst = reinterpret_cast<uint16_t*>(sm + pl.o_w[i]);
+    for (int idx = threadIdx.x; idx < Nr * Kb; idx += blockDim.x) {
+      const int o = idx / Kb, k = idx - o * Kb;
+      float v = 0.f;
+      if (o < out) v = k < in ? W[o * in + k] : (k == in ? W[out * in + o] : 0.f);
+      const uint32_t byte = row_off(o, Kb) + (k >> 3) * 128 + (k & 7) * 2;
+      dst[byte >> 1] = (uint16_t)(OP::pack(v, 0.f) & 0xFFFFu);
+    }
+  }
+  float* s = reinterpret_cast<float*>(sm + pl.o_small);
+  const int HP = pl.HP, w1 = pl.w[1];
+  const float* W0 = P + pl.off[0];
+  for (int o = threadIdx.x; o < HP; o += blockDim.x) {
+    s[o] = o < w1 ? W0[o * 2] : 0.f;
+    s[HP + o] = o < w1 ? W0[o * 2 + 1] : 0.f;
+    s[2 * HP + o] = o < w1 ? W0[w1 * 2 + o] : 0.f;
+    const int win = pl.w[L - 1];
+    s[3 * HP + o] = o < win ? P[pl.off[L - 1] + o] : 0.f;
+  }
+  if (threadIdx.x == 0) s[4 * HP] = P[pl.off[L - 1] + pl.w[L - 1]];
+}
+
+__device__ __forceinline__ void point_xy(const TcArgs& a, int64_t gp, float& x, float& y) {
+  x = 0.f; y = 0.f;
+  if (gp < a.P_mesh) { x = (float)a.Xm[2 * gp]; y = (float)a.Xm[2 * gp + 1]; }
+  else if (gp < a.P_tot) { x = (float)a.Xe[2 * (gp - a.P_mesh)]; y = (float)a.Xe[2 * (gp - a.P_mesh) + 1]; }
+}
+
+// Layer 0 on CUDA cores: H_0 row p (3 streams), this thread's column half.
+template <int HP, class OP>
+__device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_small, float x, float y, int p,
+                                             int cbase, uint8_t* buf) {
+  const int K0 = pl.WP[0], w1 = pl.w[1];
+#pragma unroll
+  for (int lc = 0; lc < HP / 32; ++lc) {
+    const int c0 = cbase + lc * 16;
+    if (c0 >= K0) break;
+    uint32_t pv[8], px[8], py[8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      float tv[2], tx[2], ty[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o = c0 + j + h;
+        const float wx = s_small[o], wy = s_small[HP + o];
+        const float t = tanh_fast(fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o])));
+        const float sd = fmaf(-t, t, 1.f);
+        tv[h] = o == w1 ? 1.f : t;
+        tx[h] = o == w1 ? 0.f : sd * wx;
+        ty[h] = o == w1 ? 0.f : sd * wy;
+      }
+      pv[j >> 1] = OP::pack(tv[0], tv[1]);
+      px[j >> 1] = OP::pack(tx[0], tx[1]);
+      py[j >> 1] = OP::pack(ty[0], ty[1]);
+    }
+    st16(buf, K0, p, c0, pv);
+    st16(buf + 256 * K0, K0, p, c0, px);
+    st16(buf + 512 * K0, K0, p, c0, py);
+  }
+}
+
+// Forward MMAs of map i: D_s (columns s*HP) = H_{i-1,s} W_i^T, K = Kin, N = Nout.
+__device__ __forceinline__ void issue_fwd(uint32_t fmt, uint32_t tD, uint32_t abuf, uint32_t wbuf, int Kin, int Nout,
+                                          int HP) {
+  const uint32_t id = idesc_f16(fmt, 128, Nout, 0, 0);
+  for (int s = 0; s < 3; ++s)
+    for (int kk = 0; kk < Kin / 16; ++kk) {
+      const uint64_t ad = sdesc(abuf + s * 256 * Kin + kk * 256, 128, Kin * 16);
+      const uint64_t bd = sdesc(wbuf + kk * 256, 128, Kin * 16);
+      mma_bf16(tD + s * HP, ad, bd, id, kk > 0);
+    }
+}
+
+// Tbar_s (columns s*HP) = Zbar_s W_i: A = Zbar (K-major, K = Nout), B = W_i read MN-major (N = Kin).
+__device__ __forceinline__ void issue_tbar(uint32_t fmt, uint32_t tD, uint32_t zbuf, uint32_t wbuf, int Kin, int Nout,
+                                           int HP) {
+  const uint32_t id = idesc_f16(fmt, 128, Kin, 0, 1);
+  for (int s = 0; s < 3; ++s)
+    for (int kk = 0; kk < Nout / 16; ++kk) {
+      const uint64_t ad = sdesc(zbuf + s * 256 * Nout + kk * 256, 128, Nout * 16);
+      const uint64_t bd = sdesc(wbuf + kk * 2 * Kin * 16, Kin * 16, 128);
+      mma_bf16(tD + s * HP, ad, bd, id, kk > 0);
+    }
+}
+
+// Wbar (M = 64 rows o, N = Nb) += sum over streams and points of Zbar^T B,
+// both read MN-major; K runs over 3 streams x 128 points.
+__device__ __forceinline__ void issue_wbar(uint32_t fmt, uint32_t tW, uint32_t zbuf, int Kz, uint32_t bbuf, int Kb,
+                                           bool first) {
+  const uint32_t id = idesc_f16(fmt, 64, Kb, 1, 1);
+  for (int s = 0; s < 3; ++s)
+    for (int ps = 0; ps < kTile / 16; ++ps) {
+      const uint64_t ad = sdesc(zbuf + s * 256 * Kz + ps * 2 * Kz * 16, Kz * 16, 128);
+      const uint64_t bd = sdesc(bbuf + s * 256 * Kb + ps * 2 * Kb * 16, Kb * 16, 128);
+      mma_bf16(tW, ad, bd, id, (first && s == 0 && ps == 0) ? 0u : 1u);
+    }
+}
+
+// ------------------------------------------------------------------ forward kernel
+// One activation tile, updated in place: once map i's MMAs have completed,
+// H_{i-1} is dead and the epilogue overwrites it with H_i.
+template <int HP, class OP>
+__global__ void __launch_bounds__(kTcThreads, 1) mlp_fwd_tc(TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const TcPlan& pl = a.pl;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q4 = warp & 3, half = warp >> 2;
+  const int p = q4 * 32 + lane;                 // point (row / TMEM lane)
+  const int cbase = half * (HP / 2);            // this thread's column half
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + pl.o_bar);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 8);
+  const float* s_small = reinterpret_cast<const float*>(sm + pl.o_small);
+  float* s_red = reinterpret_cast<float*>(sm + pl.o_red);
+  uint8_t* buf = sm + pl.o_buf[0];
+  if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_load_weights<OP>(pl, a.params, sm);
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tD = *s_tmem;
+  const uint32_t tRow = tD + ((uint32_t)(q4 * 32) << 16);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int L = pl.L;
+  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    const int64_t gp = tile * kTile + p;
+    float x, y;
+    point_xy(a, gp, x, y);
+    float u = 0.f, ux = 0.f, uy = 0.f;          // output-layer partial sums over this thread's columns
+    if (L == 2) {   // one hidden layer: output straight from layer 0
+      for (int o = cbase; o < min(pl.w[1], cbase + HP / 2); ++o) {
+        const float wx = s_small[o], wy = s_small[HP + o];
+        const float t = tanh_fast(fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o])));
+        const float sd = fmaf(-t, t, 1.f), wl = s_small[3 * HP + o];
+        u = fmaf(wl, t, u); ux = fmaf(wl, sd * wx, ux); uy = fmaf(wl, sd * wy, uy);
+      }
+    } else {
+      layer0_store<HP, OP>(pl, s_small, x, y, p, cbase, buf);
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      for (int i = 1; i <= L - 2; ++i) {
+        const int Kin = pl.WP[i - 1], Nout = pl.WP[i];
+        if (tid == 0) {
+          tc_fence_after();
+          issue_fwd(OP::fmt, tD, su32(buf), su32(sm + pl.o_w[i]), Kin, Nout, HP);
+          mma_commit(bar);
+        }
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) { failed = true; if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); break; }
+        tc_fence_after();
+        const bool last = i == L - 2;
+        const int wo = pl.w[i + 1];
+#pragma unroll
+        for (int lc = 0; lc < HP / 32; ++lc) {
+          const int c0 = cbase + lc * 16;
+          if (c0 >= Nout) break;
+          float dv[16], dx[16], dy[16];
+          tmem_ld16(tRow + c0, dv);
+          tmem_ld16(tRow + HP + c0, dx);
+          tmem_ld16(tRow + 2 * HP + c0, dy);
+          tmem_wait_ld();
+          uint32_t pv[8], px[8], py[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            float tv[2], tx[2], ty[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int o = c0 + j + h;
+              const float t = tanh_fast(dv[j + h]);
+              const float sd = fmaf(-t, t, 1.f);
+              tv[h] = o == wo ? 1.f : t;
+              tx[h] = o == wo ? 0.f : sd * dx[j + h];
+              ty[h] = o == wo ? 0.f : sd * dy[j + h];
+              if (last) {
+                const float wl = s_small[3 * HP + o];
+                u = fmaf(wl, tv[h], u); ux = fmaf(wl, tx[h], ux); uy = fmaf(wl, ty[h], uy);
+              }
+            }
+            pv[j >> 1] = OP::pack(tv[0], tv[1]);
+            px[j >> 1] = OP::pack(tx[0], tx[1]);
+            py[j >> 1] = OP::pack(ty[0], ty[1]);
+          }
+          if (!last) {
+            // H_{i-1} (the MMA's A operand) is dead: overwrite the tile with H_i
+            st16(buf, Nout, p, c0, pv);
+            st16(buf + 256 * Nout, Nout, p, c0, px);
+            st16(buf + 512 * Nout, Nout, p, c0, py);
+          }
+        }
+        if (!last) fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+      }
+      if (failed) break;
+    }
+    // combine the two column halves: u = b_L + sum over both halves
+    if (half == 1) { s_red[p * 4] = u; s_red[p * 4 + 1] = ux; s_red[p * 4 + 2] = uy; }
+    __syncthreads();
+    if (half == 0 && gp < a.P_tot) {
+      a.U[gp] = s_small[4 * HP] + u + s_red[p * 4];
+      a.U[a.P_tot + gp] = ux + s_red[p * 4 + 1];
+      a.U[2 * a.P_tot + gp] = uy + s_red[p * 4 + 2];
+    }
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tD, pl.tmem_cols);
+}
+
+// ------------------------------------------------------------------ reverse kernel
+template <int HP, class OP>
+__global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  const TcPlan& pl = a.pl;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q4 = warp & 3, half = warp >> 2;
+  const int p = q4 * 32 + lane;                 // point (row / TMEM lane)
+  const int cbase = half * (HP / 2);            // this thread's column half
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + pl.o_bar);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 8);
+  const float* s_small = reinterpret_cast<const float*>(sm + pl.o_small);
+  uint8_t* xbuf = sm + pl.o_x;
+  uint8_t* zb = sm + pl.o_z;
+  if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_load_weights<OP>(pl, a.params, sm);
+  if (half == 0) {  // layer-0 input tile: streams d/dx and d/dy are the constant unit vectors
+    uint32_t ex[8] = {OP::pack(1.f, 0.f), 0, 0, 0, 0, 0, 0, 0};
+    uint32_t ey[8] = {OP::pack(0.f, 1.f), 0, 0, 0, 0, 0, 0, 0};
+    st16(xbuf + 256 * 16, 16, p, 0, ex);
+    st16(xbuf + 512 * 16, 16, p, 0, ey);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tD = *s_tmem;
+  const uint32_t tRow = tD + ((uint32_t)(q4 * 32) << 16);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int L = pl.L;
+  uint32_t wfirst = 0xFFFFFFFFu;   // bit i: Wbar_i accumulator not yet written (thread 0)
+  float accL[HP / 2];              // output-layer weight gradient, this thread's columns and points
+#pragma unroll
+  for (int k = 0; k < HP / 2; ++k) accL[k] = 0.f;
+  int bufH[2] = {-1, -1};
+  const float sc = seed_scale(a.seed_absmax);   // adjoint scale (1 for BF16)
+  const double inv_sc = 1.0 / (double)sc;
+
+  auto sync_mma = [&]() -> bool {   // wait for the committed MMAs (all threads)
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1;
+    if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); return false; }
+    tc_fence_after();
+    return true;
+  };
+  auto publish = [&]() {            // make this thread's shared stores visible to the tensor core
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+  };
+  auto issue_fwd_map = [&](int i) {
+    if (tid == 0) {
+      tc_fence_after();
+      issue_fwd(OP::fmt, tD, su32(sm + pl.o_buf[(i - 1) & 1]), su32(sm + pl.o_w[i]), pl.WP[i - 1], pl.WP[i], HP);
+      mma_commit(bar);
+    }
+  };
+  // forward epilogue of hidden map i from D into activation tile `ob`
+  auto fwd_epilogue_store = [&](int i, uint8_t* ob) {
+    const int Nout = pl.WP[i], wo = pl.w[i + 1];
+#pragma unroll
+    for (int lc = 0; lc < HP / 32; ++lc) {
+      const int c0 = cbase + lc * 16;
+      if (c0 >= Nout) break;
+      float dv[16], dx[16], dy[16];
+      tmem_ld16(tRow + c0, dv);
+      tmem_ld16(tRow + HP + c0, dx);
+      tmem_ld16(tRow + 2 * HP + c0, dy);
+      tmem_wait_ld();
+      uint32_t pv[8], px[8], py[8];
+#pragma unroll
+      for (int j = 0; j < 16; j += 2) {
+        float tv[2], tx[2], ty[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int o = c0 + j + h;
+          const float t = tanh_fast(dv[j + h]);
+          const float sd = fmaf(-t, t, 1.f);
+          tv[h] = o == wo ? 1.f : t;
+          tx[h] = o == wo ? 0.f : sd * dx[j + h];
+          ty[h] = o == wo ? 0.f : sd * dy[j + h];
+        }
+        pv[j >> 1] = OP::pack(tv[0], tv[1]);
+        px[j >> 1] = OP::pack(tx[0], tx[1]);
+        py[j >> 1] = OP::pack(ty[0], ty[1]);
+      }
+      st16(ob, Nout, p, c0, pv);
+      st16(ob + 256 * Nout, Nout, p, c0, px);
+      st16(ob + 512 * Nout, Nout, p, c0, py);
+    }
+  };
+  // recompute H_0 .. H_upto into the two activation tiles (H_j -> buf[j & 1])
+  auto recompute = [&](int upto, float x, float y) -> bool {
+    layer0_store<HP, OP>(pl, s_small, x, y, p, cbase, sm + pl.o_buf[0]);
+    publish();
+    for (int j = 1; j <= upto; ++j) {
+      issue_fwd_map(j);
+      if (!sync_mma()) return false;
+      fwd_epilogue_store(j, sm + pl.o_buf[j & 1]);
+      publish();
+    }
+    bufH[0] = upto >= 1 ? ((upto & 1) == 0 ? upto : upto - 1) : 0;
+    bufH[1] = upto >= 1 ? ((upto & 1) == 1 ? upto : upto - 1) : -1;
+    return true;
+  };
+
+  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    const int64_t gp = tile * kTile + p;
+    float x, y;
+    point_xy(a, gp, x, y);
+    const bool live = gp < a.P_tot;
+    const float su = live ? sc * a.UB[gp] : 0.f;
+    const float sx = live ? sc * a.UB[a.P_tot + gp] : 0.f;
+    const float sy = live ? sc * a.UB[2 * a.P_tot + gp] : 0.f;
+    if (half == 0) {
+      uint32_t xr[8] = {OP::pack(x, y), OP::pack(1.f, 0.f), 0, 0, 0, 0, 0, 0};
+      st16(xbuf, 16, p, 0, xr);
+    }
+    // ---- forward recompute; the last hidden map's epilogue applies the output
+    //      layer and the seeds and writes Zbar_{L-2} (its H is never stored)
+    const int last = L - 2;
+    if (last >= 1) {
+      layer0_store<HP, OP>(pl, s_small, x, y, p, cbase, sm + pl.o_buf[0]);
+      publish();
+      for (int i = 1; i < last; ++i) {
+        issue_fwd_map(i);
+        if (!sync_mma()) { failed = true; break; }
+        fwd_epilogue_store(i, sm + pl.o_buf[i & 1]);
+        publish();
+      }
+      if (failed) break;
+      issue_fwd_map(last);
+      if (!sync_mma()) { failed = true; break; }
+    }
+    {
+      const int Nout = pl.WP[last], wo = pl.w[last + 1];
+#pragma unroll
+      for (int lc = 0; lc < HP / 32; ++lc) {
+        const int c0 = cbase + lc * 16;
+        if (c0 >= Nout) break;
+        float dv[16], dx[16], dy[16];
+        if (last >= 1) {
+          tmem_ld16(tRow + c0, dv);
+          tmem_ld16(tRow + HP + c0, dx);
+          tmem_ld16(tRow + 2 * HP + c0, dy);
+          tmem_wait_ld();
+        } else {      // single hidden layer: pre-activations from layer 0 on CUDA cores
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int o = c0 + j;
+            const float wx = s_small[o], wy = s_small[HP + o];
+            dv[j] = fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o]));
+            dx[j] = wx;
+            dy[j] = wy;
+          }
+        }
+        uint32_t pv[8], px[8], py[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          float zv[2], zx[2], zy[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int o = c0 + j + h;
+            float t = tanh_fast(dv[j + h]);
+            float sd = fmaf(-t, t, 1.f);
+            float tx = sd * dx[j + h], ty = sd * dy[j + h];
+            if (o == wo) { t = 1.f; tx = 0.f; ty = 0.f; sd = 0.f; }
+            float& acc = accL[lc * 16 + j + h];
+            acc = fmaf(su, t, fmaf(sx, tx, fmaf(sy, ty, acc)));
+            const float wl = s_small[3 * HP + o];
+            const float bv = wl * su, bx = wl * sx, by = wl * sy;
+            zv[h] = sd * bv - 2.f * t * (tx * bx + ty * by);
+            zx[h] = sd * bx;
+            zy[h] = sd * by;
+          }
+          pv[j >> 1] = OP::pack(zv[0], zv[1]);
+          px[j >> 1] = OP::pack(zx[0], zx[1]);
+          py[j >> 1] = OP::pack(zy[0], zy[1]);
+        }
+        st16(zb, Nout, p, c0, pv);
+        st16(zb + 256 * Nout, Nout, p, c0, px);
+        st16(zb + 512 * Nout, Nout, p, c0, py);
+      }
+    }
+    publish();
+    // tiles holding H after the forward: H_j in buf[j & 1] for the two highest stored j
+    bufH[0] = -1; bufH[1] = -1;
+    if (last - 1 >= 0) bufH[(last - 1) & 1] = last - 1;
+    if (last - 2 >= 0) bufH[(last - 2) & 1] = last - 2;
+    // ---- reverse, map by map from the top
+    for (int i = last; i >= 0 && !failed; --i) {
+      uint32_t bsrc;
+      int Kb;
+      if (i >= 1) {
+        if (bufH[(i - 1) & 1] != i - 1) {
+          if (!recompute(i - 1, x, y)) { failed = true; break; }
+        }
+        bsrc = su32(sm + pl.o_buf[(i - 1) & 1]);
+        Kb = pl.WP[i - 1];
+      } else {
+        bsrc = su32(xbuf);
+        Kb = 16;
+      }
+      if (tid == 0) {
+        tc_fence_after();
+        issue_wbar(OP::fmt, tD + pl.c_wbar[i], su32(zb), pl.WP[i], bsrc, Kb, (wfirst >> i) & 1u);
+        wfirst &= ~(1u << i);
+        if (i >= 1) issue_tbar(OP::fmt, tD, su32(zb), su32(sm + pl.o_w[i]), pl.WP[i - 1], pl.WP[i], HP);
+        mma_commit(bar);
+      }
+      if (!sync_mma()) { failed = true; break; }
+      if (i >= 1) {
+        // Zbar_{i-1} from Tbar_{i-1} (tensor memory) and H_{i-1} (shared tile), tanh rule
+        const int K = pl.WP[i - 1];
+        const uint8_t* hb = sm + pl.o_buf[(i - 1) & 1];
+#pragma unroll
+        for (int lc = 0; lc < HP / 32; ++lc) {
+          const int c0 = cbase + lc * 16;
+          if (c0 >= K) break;
+          float bv[16], bx[16], by[16], hv[16], hx[16], hy[16];
+          tmem_ld16(tRow + c0, bv);
+          tmem_ld16(tRow + HP + c0, bx);
+          tmem_ld16(tRow + 2 * HP + c0, by);
+          ld16<OP>(hb, K, p, c0, hv);
+          ld16<OP>(hb + 256 * K, K, p, c0, hx);
+          ld16<OP>(hb + 512 * K, K, p, c0, hy);
+          tmem_wait_ld();
+          uint32_t pv[8], px[8], py[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            float zv[2], zx[2], zy[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float t = hv[j + h], sd = fmaf(-t, t, 1.f);
+              zv[h] = sd * bv[j + h] - 2.f * t * (hx[j + h] * bx[j + h] + hy[j + h] * by[j + h]);
+              zx[h] = sd * bx[j + h];
+              zy[h] = sd * by[j + h];
+            }
+            pv[j >> 1] = OP::pack(zv[0], zv[1]);
+            px[j >> 1] = OP::pack(zx[0], zx[1]);
+            py[j >> 1] = OP::pack(zy[0], zy[1]);
+          }
+          st16(zb, K, p, c0, pv);
+          st16(zb + 256 * K, K, p, c0, px);
+          st16(zb + 512 * K, K, p, c0, py);
+        }
+        publish();
+      } else {
+        tc_fence_before();
+        __syncthreads();
+      }
+    }
+  }
+  // ---- write this CTA's gradient partials
+  uint32_t* s_flags = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 12);
+  if (tid == 0) *s_flags = wfirst;          // accumulators never written by this CTA
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t never_mask = *s_flags;
+  double* g = a.gpart + (size_t)blockIdx.x * pl.n_params;
+  if (!failed) {
+    if (half == 0) {
+      // hidden maps 0..L-2 from tensor memory (M = 64 layout: row o in lane (o/16)*32 + o%16)
+      const int o = q4 * 16 + lane;
+      for (int i = 0; i <= L - 2; ++i) {
+        const int Kb = i >= 1 ? pl.WP[i - 1] : 16;
+        const int in = pl.w[i], out = pl.w[i + 1];
+        const bool never = (never_mask >> i) & 1u;
+        for (int c0 = 0; c0 < Kb; c0 += 16) {
+          float v[16];
+          tmem_ld16(tRow + pl.c_wbar[i] + c0, v);
+          tmem_wait_ld();
+          if (lane < 16 && o < out) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int k = c0 + j;
+              const double val = never ? 0.0 : (double)v[j] * inv_sc;
+              if (k < in) g[pl.off[i] + o * in + k] = val;
+              else if (k == in) g[pl.off[i] + out * in + o] = val;
+            }
+          }
+        }
+      }
+    }
+  } else {
+    for (int i = tid; i < pl.n_params; i += kTcThreads) g[i] = 0.0;
+  }
+  // output layer: reduce accL over the CTA's 128 points in fixed order
+  tc_fence_before();
+  __syncthreads();
+  float* scratch = reinterpret_cast<float*>(sm + pl.o_buf[0]);   // [128][HP]
+#pragma unroll
+  for (int k = 0; k < HP / 2; ++k) scratch[p * HP + cbase + k] = accL[k];
+  __syncthreads();
+  if (tid < HP) {
+    double sum = 0.0;
+    for (int t = 0; t < kTile; ++t) sum += (double)scratch[t * HP + tid];
+    const int win = pl.w[L - 1];
+    if (tid <= win) g[pl.off[L - 1] + tid] = failed ? 0.0 : sum * inv_sc;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tD, pl.tmem_cols);
+}
+
+// ------------------------------------------------------------------ host side
+bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
+  const MlpShape& s = ep.shape;
+  if (ep.prec != FV_BF16 && ep.prec != FV_FP16) return false;
+  if (s.L < 2) return false;
+  p->L = s.L;
+  p->n_params = s.n_params;
+  int HP = 16;
+  for (int i = 0; i <= s.L; ++i) p->w[i] = s.w[i];
+  for (int i = 0; i < s.L; ++i) p->off[i] = s.off[i];
+  for (int i = 0; i + 1 < s.L; ++i) {
+    p->WP[i] = ru16(s.w[i + 1] + 1);
+    HP = std::max(HP, p->WP[i]);
+  }
+  if (HP > 64) return false;
+  HP = HP <= 32 ? 32 : 64;
+  p->HP = HP;
+  int o = 0;
+  for (int i = 1; i <= s.L - 2; ++i) {
+    p->o_w[i] = o;
+    o += p->WP[i] * p->WP[i - 1] * 2;
+  }
+  o = (o + 127) & ~127;
+  p->o_small = o; o += (4 * HP + 4) * 4;
+  o = (o + 127) & ~127;
+  const int tile_bytes = 3 * kTile * HP * 2;
+  p->o_buf[0] = o; o += tile_bytes;
+  if (reverse) {
+    p->o_buf[1] = o; o += tile_bytes;
+    p->o_z = o; o += tile_bytes;
+    p->o_x = o; o += 3 * kTile * 16 * 2;
+    o += 512;   // the 64-row weight-gradient read of a 32-wide adjoint tile runs past its end
+  } else {
+    p->o_buf[1] = p->o_buf[0];
+    p->o_z = p->o_x = 0;
+  }
+  p->o_red = o; o += kTile * 4 * 4;
+  p->o_bar = o; o += 16;
+  p->smem = (o + 127) & ~127;
+  int cols = 3 * HP;
+  if (reverse) {
+    for (int i = 1; i <= s.L - 2; ++i) { p->c_wbar[i] = cols; cols += HP; }
+    p->c_wbar[0] = cols; cols += 16;
+  }
+  int t = 32;
+  while (t < cols) t *= 2;
+  if (t > 512) return false;
+  p->tmem_cols = t;
+  return true;
+}
+
+// Resident CTAs per SM: the hardware occupancy (registers, shared memory)
+// capped so that their tensor-memory allocations fit in 512 columns.
+template <int HP, class OP>
+int tc_ctas_per_sm(const TcPlan& p, bool reverse) {
+  int n = 0;
+  cudaError_t e;
+  if (reverse) {
+    cudaFuncSetAttribute(mlp_bwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_bwd_tc<HP, OP>, kTcThreads, p.smem);
+  } else {
+    cudaFuncSetAttribute(mlp_fwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_fwd_tc<HP, OP>, kTcThreads, p.smem);
+  }
+  if (e != cudaSuccess || n < 1) n = 1;
+  return std::max(1, std::min(n, 512 / p.tmem_cols));
+}
+
+int tc_grid(fv_ctx ctx, const TcPlan& p, bool reverse, bool fp16, int64_t P_tot) {
+  const int64_t n_tiles = (P_tot + kTile - 1) / kTile;
+  const int per = p.HP == 32 ? (fp16 ? tc_ctas_per_sm<32, OpF16>(p, reverse) : tc_ctas_per_sm<32, OpBF16>(p, reverse))
+                             : (fp16 ? tc_ctas_per_sm<64, OpF16>(p, reverse) : tc_ctas_per_sm<64, OpBF16>(p, reverse));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)ctx->n_sm * per));
+}
+
+template <int HP, class OP>
+int launch_tc(fv_ctx ctx, const TcArgs& a, bool reverse, int grid) {
+  cudaError_t e;
+  if (reverse) {
+    e = cudaFuncSetAttribute(mlp_bwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    if (e == cudaSuccess) mlp_bwd_tc<HP, OP><<<grid, kTcThreads, a.pl.smem, ctx->stream>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(mlp_fwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    if (e == cudaSuccess) mlp_fwd_tc<HP, OP><<<grid, kTcThreads, a.pl.smem, ctx->stream>>>(a);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("tensor-core MLP launch failed: %s", cudaGetErrorString(e));
+    return FV_ERR_CUDA;
+  }
+  return FV_OK;
+}
+
+int launch_tc_any(fv_ctx ctx, const TcArgs& a, bool reverse, bool fp16, int grid) {
+  if (a.pl.HP == 32) return fp16 ? launch_tc<32, OpF16>(ctx, a, reverse, grid) : launch_tc<32, OpBF16>(ctx, a, reverse, grid);
+  return fp16 ? launch_tc<64, OpF16>(ctx, a, reverse, grid) : launch_tc<64, OpBF16>(ctx, a, reverse, grid);
+}
+
+}  // namespace
+
+bool tc_supported(const EvalPlan& pl) {
+  TcPlan p;
+  return make_tc_plan(pl, true, &p) && p.smem <= 227 * 1024;
+}
+
+int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl) {
+  TcPlan p;
+  if (!make_tc_plan(pl, true, &p)) return -FV_ERR_UNSUPPORTED;
+  return tc_grid(ctx, p, true, pl.prec == FV_FP16, pl.P_tot);
+}
 
 int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xm, const double* Xe,
                       void* U) {
-  (void)ctx; (void)pl; (void)params; (void)Xm; (void)Xe; (void)U;
-  set_error("tensor-core MLP path not available");
-  return FV_ERR_UNSUPPORTED;
+  TcArgs a;
+  if (!make_tc_plan(pl, false, &a.pl)) { set_error("tensor-core path: unsupported network"); return FV_ERR_UNSUPPORTED; }
+  a.params = static_cast<const float*>(params);
+  a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot;
+  a.U = static_cast<float*>(U); a.UB = nullptr; a.gpart = nullptr; a.seed_absmax = nullptr; a.err = ctx->err_dev;
+  const int grid = tc_grid(ctx, a.pl, false, pl.prec == FV_FP16, pl.P_tot);
+  cudaEvent_t ta;
+  time_begin(ctx, K_MLP_FWD_TC, &ta);
+  const int rc = launch_tc_any(ctx, a, false, pl.prec == FV_FP16, grid);
+  time_end(ctx, K_MLP_FWD_TC, ta);
+  return rc;
 }
 
 int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xm, const double* Xe,
-                      const void* UB, double* gpart, int* nb) {
-  (void)ctx; (void)pl; (void)params; (void)Xm; (void)Xe; (void)UB; (void)gpart; (void)nb;
-  set_error("tensor-core MLP path not available");
-  return FV_ERR_UNSUPPORTED;
+                      const void* UB, double* gpart, int* nb, const float* seed_absmax) {
+  TcArgs a;
+  if (!make_tc_plan(pl, true, &a.pl)) { set_error("tensor-core path: unsupported network"); return FV_ERR_UNSUPPORTED; }
+  a.params = static_cast<const float*>(params);
+  a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot;
+  a.U = nullptr; a.UB = static_cast<const float*>(UB); a.gpart = gpart; a.err = ctx->err_dev;
+  a.seed_absmax = pl.prec == FV_FP16 ? seed_absmax : nullptr;
+  const int grid = mlp_bwd_tc_blocks(ctx, pl);
+  *nb = grid;
+  cudaEvent_t ta;
+  time_begin(ctx, K_MLP_BWD_TC, &ta);
+  const int rc = launch_tc_any(ctx, a, true, pl.prec == FV_FP16, grid);
+  time_end(ctx, K_MLP_BWD_TC, ta);
+  return rc;
 }
 
 }  // namespace fv
