@@ -168,6 +168,33 @@ int fv_loss(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp
 int fv_loss_grad(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
                  const void* params_dev, const fv_eval_opts* opts, void* grad_dev, double* out_dev);
 
+/* Size of the fixed scratch area used by fv_loss_grad_noalloc (32 MiB). */
+#define FV_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* fv_loss_grad for callers that must not allocate device memory.  (This is a
+ * service of the library; the paper has no counterpart.)  Some callers cannot
+ * call cudaMalloc: code running in a host callback enqueued on a stream, which
+ * may not make CUDA API calls; programs whose device memory is owned by a
+ * framework pool that forbids raw allocations; and latency-critical loops that
+ * cannot afford cudaMalloc's implicit device-wide synchronisation.  This entry
+ * point computes exactly what fv_loss_grad computes, with the same arguments,
+ * but keeps every temporary in one fixed area of FV_NOALLOC_SCRATCH_BYTES that
+ * is compiled into the library: each device that loads the library holds that
+ * area until the process exits.  Nothing is allocated per call.
+ *   - Size limit: problems whose temporaries exceed the area (roughly a million
+ *     quadrature points in FP32, fewer in FP64 or with large networks) are
+ *     rejected with FV_ERR_UNSUPPORTED and a message giving both sizes.
+ *   - Set-up: the first call on a device looks up the area's device address
+ *     (once per device); make that first call before any stream capture.
+ *   - Sharing: every call on a device uses the same area, and the area keeps
+ *     the last call's contents.  Calls whose kernels overlap on the GPU (for
+ *     example on two streams, or from two contexts) race on it; issue them one
+ *     after another.  The per-kernel timing of fv_ctx_enable_timing is not
+ *     recorded for these calls.
+ * Arguments, layout, outputs and other errors as for fv_loss_grad. */
+int fv_loss_grad_noalloc(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                         const void* params_dev, const fv_eval_opts* opts, void* grad_dev, double* out_dev);
+
 /* Inspection: one loss + gradient evaluation that also copies out its
  * intermediates (synchronises the stream):
  *   U_dev  [3][P_tot]   u, du/dx, du/dy at the quadrature points then the boundary and sensor points

@@ -66,6 +66,7 @@ SIGNATURES = {
     "fv_bc_destroy": [_vp],
     "fv_loss": [_vp, _vp, _vp, _vp, C.POINTER(fv_mlp_desc), _vp, C.POINTER(fv_eval_opts), _vp],
     "fv_loss_grad": [_vp, _vp, _vp, _vp, C.POINTER(fv_mlp_desc), _vp, C.POINTER(fv_eval_opts), _vp, _vp],
+    "fv_loss_grad_noalloc": [_vp, _vp, _vp, _vp, C.POINTER(fv_mlp_desc), _vp, C.POINTER(fv_eval_opts), _vp, _vp],
     "fv_eval_intermediates": [_vp, _vp, _vp, _vp, C.POINTER(fv_mlp_desc), _vp, C.POINTER(fv_eval_opts), _vp, _vp,
                               _vp, _vp],
     "fv_mlp_eval": [_vp, C.POINTER(fv_mlp_desc), _vp, C.c_int, C.c_int, _vp, _vp],

@@ -223,6 +223,16 @@ class Problem:
                C.byref(self.net.desc), _ptr(params), C.byref(o), _ptr(grad), _ptr(out))
         return out, grad
 
+    def loss_grad_noalloc(self, params: torch.Tensor, grad: torch.Tensor, out: torch.Tensor):
+        """fv_loss_grad_noalloc: as loss_grad, with every temporary in the
+        library's fixed scratch area (for callers that cannot allocate device
+        memory); grad and out must be supplied."""
+        self._check_params(params)
+        o = self.opts()
+        N.call("fv_loss_grad_noalloc", self.ctx.h, self.mesh.h, self.forcing.h, self.bc.h if self.bc else None,
+               C.byref(self.net.desc), _ptr(params), C.byref(o), _ptr(grad), _ptr(out))
+        return out, grad
+
     def intermediates(self, params: torch.Tensor):
         """(out, U [3][P_tot], UB [3][P_tot], R [n_e][T*T]) of one evaluation."""
         self._check_params(params)

@@ -228,9 +228,21 @@ struct WsLayout {
 };
 
 // The core evaluation shared by fv_loss, fv_loss_grad and fv_inverse_step.
+// Restores a context's timing switch on scope exit.
+struct TimingOff {
+  fv_ctx ctx;
+  bool saved;
+  explicit TimingOff(fv_ctx c, bool off) : ctx(c), saved(c ? c->timing : false) { if (c && off) c->timing = false; }
+  ~TimingOff() { if (ctx) ctx->timing = saved; }
+};
+
+// fixed_ws: when given, all temporaries go to this caller-supplied device area
+// of fixed_ws_bytes (no workspace growth, no timing events).
 int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp, const void* params,
              const fv_eval_opts* opts, const double* eps_dev, bool want_grad, void* grad, double* out,
-             void* U_copy = nullptr, void* UB_copy = nullptr, double* R_out = nullptr) {
+             void* U_copy = nullptr, void* UB_copy = nullptr, double* R_out = nullptr, void* fixed_ws = nullptr,
+             size_t fixed_ws_bytes = 0) {
+  TimingOff timing_guard(ctx, fixed_ws != nullptr);
   MlpShape sh;
   int rc = check_eval(ctx, mesh, forcing, bc, mlp, params, opts, &sh);
   if (rc) return rc;
@@ -266,8 +278,16 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   w.smax = o; o += al(16);
   w.total = o;
   void* base;
-  rc = ws_reserve(ctx, w.total, &base);
-  if (rc) return rc;
+  if (fixed_ws) {
+    if (w.total > fixed_ws_bytes) {
+      set_error("this problem needs %zu bytes of scratch; the fixed scratch area holds %zu", w.total, fixed_ws_bytes);
+      return FV_ERR_UNSUPPORTED;
+    }
+    base = fixed_ws;
+  } else {
+    rc = ws_reserve(ctx, w.total, &base);
+    if (rc) return rc;
+  }
   char* b = static_cast<char*>(base);
   void* U = b + w.U;
   void* UB = want_grad ? b + w.UB : nullptr;
@@ -445,6 +465,51 @@ extern "C" int fv_loss_grad(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc 
   FV_CHECK_ARG(out && grad, "fv_loss_grad: null output");
   if (ctx) FV_CUDA_TRY(cudaSetDevice(ctx->device));
   return evaluate(ctx, mesh, forcing, bc, mlp, params, opts, nullptr, true, grad, out);
+}
+
+// ---------------------------------------------------------------- evaluation without allocation
+// Scratch for fv_loss_grad_noalloc: a fixed area in the library's device
+// image, present on every device that loads the library, until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FV_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (which must be current).
+// In host code the array's name only stands in for the symbol, so the
+// address is looked up once per device and cached.
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) {
+    set_error("fv_loss_grad_noalloc: device %d out of range", device);
+    return FV_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("fv_loss_grad_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return FV_ERR_CUDA;
+    }
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return FV_OK;
+}
+}  // namespace
+
+extern "C" int fv_loss_grad_noalloc(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                                    const void* params, const fv_eval_opts* opts, void* grad, double* out) {
+  clear_error();
+  FV_CHECK_ARG(ctx && out && grad, "fv_loss_grad_noalloc: null argument");
+  FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(ctx->device, &scratch);
+  if (rc) return rc;
+  return evaluate(ctx, mesh, forcing, bc, mlp, params, opts, nullptr, true, grad, out, nullptr, nullptr, nullptr,
+                  scratch, FV_NOALLOC_SCRATCH_BYTES);
 }
 
 extern "C" int fv_eval_intermediates(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,

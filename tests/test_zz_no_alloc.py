@@ -1,0 +1,75 @@
+"""fv_loss_grad_noalloc: loss and gradient for callers that cannot allocate
+device memory -- code in a host callback enqueued on a stream (which may not
+call the CUDA API), programs whose device memory belongs to a framework pool
+that forbids raw allocations, and latency-critical loops that cannot pay for
+cudaMalloc's device-wide synchronisation.  The entry point keeps its
+temporaries in a fixed scratch area compiled into the library; it must give
+what fv_loss_grad gives, call after call, and allocate nothing per call.
+
+This file is collected last on purpose (its name sorts after the others).
+"""
+import numpy as np
+import pytest
+
+import fv_inputs as fi
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "fp16": 2e-2}
+
+
+def rel(a, b):
+    a = np.asarray(a.cpu() if hasattr(a, "cpu") else a, dtype=np.float64)
+    b = np.asarray(b.cpu() if hasattr(b, "cpu") else b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_12063_b300 import build
+    build.build()
+    from paper_2404_12063_b300 import api as A
+    return A
+
+
+@pytest.mark.parametrize("k,precision", [(1, "fp64"), (2, "fp32"), (2, "fp16")])
+def test_noalloc_matches_loss_grad_on_two_calls(api, k, precision):
+    ctx = api.Context(0)
+    prob = fi.CONFIGS[k]()
+    pb = api.problem_from_inputs(ctx, prob, precision)
+    params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+    outs = []
+    free = []
+    for _ in range(2):
+        grad = torch.full_like(params, float("nan"))
+        out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+        pb.loss_grad_noalloc(params, grad, out)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        outs.append((out.clone(), grad.clone()))
+    assert free[0] == free[1]                      # the second call allocated nothing
+    ref_out, ref_grad = pb.loss_grad(params)       # the existing entry point
+    ref_out, ref_grad = ref_out.clone(), ref_grad.clone()
+    torch.cuda.synchronize()
+    tol = TOL[precision]
+    for out, grad in outs:
+        assert torch.isfinite(out).all() and torch.isfinite(grad).all()
+        assert rel(out[:4], ref_out[:4]) < tol
+        assert rel(grad, ref_grad) < tol
+
+
+def test_noalloc_rejects_a_problem_larger_than_its_scratch(api):
+    from paper_2404_12063_b300 import FVError, _native as N
+    ctx = api.Context(0)
+    prob = fi.config4_inverse()                    # 1.6 million points: temporaries exceed the area
+    pb = api.problem_from_inputs(ctx, prob, "fp32")
+    params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(params)
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    with pytest.raises(FVError) as ei:
+        pb.loss_grad_noalloc(params, grad, out)
+    assert ei.value.code == N.FV_ERR_UNSUPPORTED
+    assert "bytes of scratch" in str(ei.value)
