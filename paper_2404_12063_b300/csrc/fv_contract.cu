@@ -475,17 +475,17 @@ int launch_t(fv_ctx ctx, const ContractArgs& a, bool pipelined, int grid, size_t
 
 }  // namespace
 
-// Stage geometry: about 48 KB of G per stage, up to 4 stages within ~200 KB.
+// Stage geometry: about 96 KB of G per stage (several elements, so that the
+// per-stage barriers are amortised over many rows), 2-4 stages within ~210 KB.
 int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, int* stages, size_t* smem) {
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
   const size_t budget = std::min<size_t>(ctx->smem_optin, 220 * 1024);
   const size_t gs = m->g_stride_bytes;
-  int E = (int)std::max<size_t>(1, (48 * 1024) / gs);
-  E = std::min(E, 32);
-  int S = 4;
-  while (S >= 2 && pipelined_smem(E * gs, S, E, m->Nq, m->Nt, rsz) > budget) {
-    if (E > 1) E = std::max(1, E / 2); else --S;
-  }
+  // as many elements per stage as fit with two stages (up to ~96 KB), then add stages while they fit
+  int E = (int)std::min<size_t>(32, std::max<size_t>(1, (96 * 1024 + gs - 1) / gs));
+  while (E > 1 && pipelined_smem(E * gs, 2, E, m->Nq, m->Nt, rsz) > budget) --E;
+  int S = pipelined_smem(E * gs, 2, E, m->Nq, m->Nt, rsz) <= budget ? 2 : 0;
+  while (S >= 2 && S < 4 && pipelined_smem(E * gs, S + 1, E, m->Nq, m->Nt, rsz) <= budget) ++S;
   if (S < 2 || E * gs > (1u << 20) - 16 || m->Nq > 128) {   // too large to stage / > 4 q-chunks: direct kernel
     *eg = 0; *stages = 0;
     *smem = (size_t)m->Nt * 8 + kWarps * 4 * 8;
@@ -493,10 +493,9 @@ int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, 
     return FV_OK;
   }
   const size_t sm = pipelined_smem(E * gs, S, E, m->Nq, m->Nt, rsz);
-  const int per_sm = std::max<int>(1, (int)(std::min<size_t>(ctx->smem_optin, 228 * 1024) / (sm + 1024)));
   const int n_groups = (m->n_e + E - 1) / E;
   *eg = E; *stages = S; *smem = sm;
-  *grid = std::min<int>(n_groups, ctx->n_sm * std::min(per_sm, 1));
+  *grid = std::min<int>(n_groups, ctx->n_sm);
   return FV_OK;
 }
 

@@ -9,9 +9,9 @@
 //            Wbar_i += sum_s Zbar_s^T H_{i-1,s}     (bias gradient from a ones column)
 //            Tbar_{i-1,s} = Zbar_s W_i
 //
-// A CTA of 256 threads handles tiles of 128 points: point p is row p of every
-// GEMM tile and lane p of tensor memory; warps w and w+4 share TMEM lane
-// quarter w and split the tile's columns between them.  All three
+// A CTA of 128 x (HP/16) threads handles tiles of 128 points: point p is row
+// p of every GEMM tile and lane p of tensor memory; warps w, w+4, ... share
+// TMEM lane quarter w and each takes one 16-column group of the tile.  All three
 // GEMMs read the same shared-memory tiles: activations are stored once in the
 // no-swizzle core-matrix layout (8 rows x 16 bytes) and addressed as K-major
 // operands (forward, Tbar) or as MN-major operands (weight gradient, and W_i
@@ -26,8 +26,10 @@
 namespace fv {
 namespace {
 
-constexpr int kTcThreads = 256;
 constexpr int kTile = 128;
+// 128 x (HP/16) threads: thread (quarter q, group g, lane l) owns point
+// p = 32 q + l (TMEM lane p) and the 16 columns [16 g, 16 g + 16).
+template <int HP> constexpr int tc_threads() { return kTile * (HP / 16); }
 constexpr uint64_t kTcWaitNs = 2000000000ull;
 
 inline int ru16(int v) { return (v + 15) & ~15; }
@@ -84,16 +86,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -144,21 +144,17 @@ __device__ __forceinline__ float tanh_fast(float x) {
 // 256*Kb bytes.
 __device__ __forceinline__ uint32_t row_off(int p, int Kb) { return (p >> 3) * (Kb * 16) + (p & 7) * 16; }
 
-__device__ __forceinline__ void st16(uint8_t* stream, int Kb, int p, int c0, const uint32_t pk[8]) {
-  uint8_t* b = stream + row_off(p, Kb) + (c0 >> 3) * 128;
-  *reinterpret_cast<uint4*>(b) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-  *reinterpret_cast<uint4*>(b + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+// 8 columns [c, c+8) of row p (one 16-byte core-matrix row segment).
+__device__ __forceinline__ void st8(uint8_t* stream, int Kb, int p, int c, const uint32_t pk[4]) {
+  *reinterpret_cast<uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 template <class OP>
-__device__ __forceinline__ void ld16(const uint8_t* stream, int Kb, int p, int c0, float v[16]) {
-  const uint8_t* b = stream + row_off(p, Kb) + (c0 >> 3) * 128;
-  const uint4 x = *reinterpret_cast<const uint4*>(b);
-  const uint4 y = *reinterpret_cast<const uint4*>(b + 128);
-  const uint32_t u[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+__device__ __forceinline__ void ld8(const uint8_t* stream, int Kb, int p, int c, float v[8]) {
+  const uint4 x = *reinterpret_cast<const uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128);
+  const uint32_t u[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-  for (int i = 0; i < 8; ++i) { v[2 * i] = OP::lo(u[i]); v[2 * i + 1] = OP::hi(u[i]); }
+  for (int i = 0; i < 4; ++i) { v[2 * i] = OP::lo(u[i]); v[2 * i + 1] = OP::hi(u[i]); }
 }
-
 // ------------------------------------------------------------------ plan
 struct TcPlan {
   int L;
@@ -241,22 +237,21 @@ __device__ __forceinline__ void point_xy(const TcArgs& a, int64_t gp, float& x, 
   else if (gp < a.P_tot) { x = (float)a.Xe[2 * (gp - a.P_mesh)]; y = (float)a.Xe[2 * (gp - a.P_mesh) + 1]; }
 }
 
-// Layer 0 on CUDA cores: H_0 row p (3 streams), this thread's column half.
-template <int HP, class OP>
+// Layer 0 on CUDA cores: H_0 row p (3 streams), this thread's 16 columns.
+template <class OP>
 __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_small, float x, float y, int p,
-                                             int cbase, uint8_t* buf) {
-  const int K0 = pl.WP[0], w1 = pl.w[1];
+                                             int c0, uint8_t* buf) {
+  const int K0 = pl.WP[0], w1 = pl.w[1], HP = pl.HP;
+  if (c0 >= K0) return;
 #pragma unroll
-  for (int lc = 0; lc < HP / 32; ++lc) {
-    const int c0 = cbase + lc * 16;
-    if (c0 >= K0) break;
-    uint32_t pv[8], px[8], py[8];
+  for (int sc = 0; sc < 16; sc += 8) {
+    uint32_t pv[4], px[4], py[4];
 #pragma unroll
-    for (int j = 0; j < 16; j += 2) {
+    for (int j = 0; j < 8; j += 2) {
       float tv[2], tx[2], ty[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int o = c0 + j + h;
+        const int o = c0 + sc + j + h;
         const float wx = s_small[o], wy = s_small[HP + o];
         const float t = tanh_fast(fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o])));
         const float sd = fmaf(-t, t, 1.f);
@@ -268,9 +263,9 @@ __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_sm
       px[j >> 1] = OP::pack(tx[0], tx[1]);
       py[j >> 1] = OP::pack(ty[0], ty[1]);
     }
-    st16(buf, K0, p, c0, pv);
-    st16(buf + 256 * K0, K0, p, c0, px);
-    st16(buf + 512 * K0, K0, p, c0, py);
+    st8(buf, K0, p, c0 + sc, pv);
+    st8(buf + 256 * K0, K0, p, c0 + sc, px);
+    st8(buf + 512 * K0, K0, p, c0 + sc, py);
   }
 }
 
@@ -315,17 +310,18 @@ __device__ __forceinline__ void issue_wbar(uint32_t fmt, uint32_t tW, uint32_t z
 // One activation tile, updated in place: once map i's MMAs have completed,
 // H_{i-1} is dead and the epilogue overwrites it with H_i.
 template <int HP, class OP>
-__global__ void __launch_bounds__(kTcThreads, 1) mlp_fwd_tc(TcArgs a) {
+__global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
+  constexpr int NG = HP / 16;
   extern __shared__ __align__(1024) uint8_t sm[];
   const TcPlan& pl = a.pl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q4 = warp & 3, half = warp >> 2;
+  const int q4 = warp & 3, grp = warp >> 2;
   const int p = q4 * 32 + lane;                 // point (row / TMEM lane)
-  const int cbase = half * (HP / 2);            // this thread's column half
+  const int c0 = grp * 16;                      // this thread's 16 columns
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + pl.o_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 8);
   const float* s_small = reinterpret_cast<const float*>(sm + pl.o_small);
-  float* s_red = reinterpret_cast<float*>(sm + pl.o_red);
+  float* s_red = reinterpret_cast<float*>(sm + pl.o_red);        // [NG][128][3]
   uint8_t* buf = sm + pl.o_buf[0];
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
@@ -349,14 +345,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fwd_tc(TcArgs a) {
     point_xy(a, gp, x, y);
     float u = 0.f, ux = 0.f, uy = 0.f;          // output-layer partial sums over this thread's columns
     if (L == 2) {   // one hidden layer: output straight from layer 0
-      for (int o = cbase; o < min(pl.w[1], cbase + HP / 2); ++o) {
+      for (int o = c0; o < min(pl.w[1], c0 + 16); ++o) {
         const float wx = s_small[o], wy = s_small[HP + o];
         const float t = tanh_fast(fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o])));
         const float sd = fmaf(-t, t, 1.f), wl = s_small[3 * HP + o];
         u = fmaf(wl, t, u); ux = fmaf(wl, sd * wx, ux); uy = fmaf(wl, sd * wy, uy);
       }
     } else {
-      layer0_store<HP, OP>(pl, s_small, x, y, p, cbase, buf);
+      layer0_store<OP>(pl, s_small, x, y, p, c0, buf);
       fence_proxy_async();
       tc_fence_before();
       __syncthreads();
@@ -373,41 +369,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fwd_tc(TcArgs a) {
         tc_fence_after();
         const bool last = i == L - 2;
         const int wo = pl.w[i + 1];
+        if (c0 < Nout) {
 #pragma unroll
-        for (int lc = 0; lc < HP / 32; ++lc) {
-          const int c0 = cbase + lc * 16;
-          if (c0 >= Nout) break;
-          float dv[16], dx[16], dy[16];
-          tmem_ld16(tRow + c0, dv);
-          tmem_ld16(tRow + HP + c0, dx);
-          tmem_ld16(tRow + 2 * HP + c0, dy);
-          tmem_wait_ld();
-          uint32_t pv[8], px[8], py[8];
+          for (int sc = 0; sc < 16; sc += 8) {
+            const int cc = c0 + sc;
+            float dv[8], dx[8], dy[8];
+            tmem_ld8(tRow + cc, dv);
+            tmem_ld8(tRow + HP + cc, dx);
+            tmem_ld8(tRow + 2 * HP + cc, dy);
+            tmem_wait_ld();
+            uint32_t pv[4], px[4], py[4];
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            float tv[2], tx[2], ty[2];
+            for (int j = 0; j < 8; j += 2) {
+              float tv[2], tx[2], ty[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int o = c0 + j + h;
-              const float t = tanh_fast(dv[j + h]);
-              const float sd = fmaf(-t, t, 1.f);
-              tv[h] = o == wo ? 1.f : t;
-              tx[h] = o == wo ? 0.f : sd * dx[j + h];
-              ty[h] = o == wo ? 0.f : sd * dy[j + h];
-              if (last) {
-                const float wl = s_small[3 * HP + o];
-                u = fmaf(wl, tv[h], u); ux = fmaf(wl, tx[h], ux); uy = fmaf(wl, ty[h], uy);
+              for (int h = 0; h < 2; ++h) {
+                const int o = cc + j + h;
+                const float t = tanh_fast(dv[j + h]);
+                const float sd = fmaf(-t, t, 1.f);
+                tv[h] = o == wo ? 1.f : t;
+                tx[h] = o == wo ? 0.f : sd * dx[j + h];
+                ty[h] = o == wo ? 0.f : sd * dy[j + h];
+                if (last) {
+                  const float wl = s_small[3 * HP + o];
+                  u = fmaf(wl, tv[h], u); ux = fmaf(wl, tx[h], ux); uy = fmaf(wl, ty[h], uy);
+                }
               }
+              pv[j >> 1] = OP::pack(tv[0], tv[1]);
+              px[j >> 1] = OP::pack(tx[0], tx[1]);
+              py[j >> 1] = OP::pack(ty[0], ty[1]);
             }
-            pv[j >> 1] = OP::pack(tv[0], tv[1]);
-            px[j >> 1] = OP::pack(tx[0], tx[1]);
-            py[j >> 1] = OP::pack(ty[0], ty[1]);
-          }
-          if (!last) {
-            // H_{i-1} (the MMA's A operand) is dead: overwrite the tile with H_i
-            st16(buf, Nout, p, c0, pv);
-            st16(buf + 256 * Nout, Nout, p, c0, px);
-            st16(buf + 512 * Nout, Nout, p, c0, py);
+            if (!last) {
+              // H_{i-1} (the MMA's A operand) is dead: overwrite the tile with H_i
+              st8(buf, Nout, p, cc, pv);
+              st8(buf + 256 * Nout, Nout, p, cc, px);
+              st8(buf + 512 * Nout, Nout, p, cc, py);
+            }
           }
         }
         if (!last) fence_proxy_async();
@@ -416,13 +413,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fwd_tc(TcArgs a) {
       }
       if (failed) break;
     }
-    // combine the two column halves: u = b_L + sum over both halves
-    if (half == 1) { s_red[p * 4] = u; s_red[p * 4 + 1] = ux; s_red[p * 4 + 2] = uy; }
+    // combine the column groups in fixed order: u = b_L + sum over groups
+    s_red[(grp * kTile + p) * 3] = u;
+    s_red[(grp * kTile + p) * 3 + 1] = ux;
+    s_red[(grp * kTile + p) * 3 + 2] = uy;
     __syncthreads();
-    if (half == 0 && gp < a.P_tot) {
-      a.U[gp] = s_small[4 * HP] + u + s_red[p * 4];
-      a.U[a.P_tot + gp] = ux + s_red[p * 4 + 1];
-      a.U[2 * a.P_tot + gp] = uy + s_red[p * 4 + 2];
+    if (grp == 0 && gp < a.P_tot) {
+      float su = s_small[4 * HP], sx = 0.f, sy = 0.f;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        su += s_red[(g * kTile + p) * 3];
+        sx += s_red[(g * kTile + p) * 3 + 1];
+        sy += s_red[(g * kTile + p) * 3 + 2];
+      }
+      a.U[gp] = su;
+      a.U[a.P_tot + gp] = sx;
+      a.U[2 * a.P_tot + gp] = sy;
     }
     __syncthreads();
   }
@@ -434,13 +440,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_fwd_tc(TcArgs a) {
 
 // ------------------------------------------------------------------ reverse kernel
 template <int HP, class OP>
-__global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
+__global__ void __launch_bounds__(tc_threads<HP>(), 1) mlp_bwd_tc(TcArgs a) {
+  constexpr int NT = tc_threads<HP>();
   extern __shared__ __align__(1024) uint8_t sm[];
   const TcPlan& pl = a.pl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q4 = warp & 3, half = warp >> 2;
+  const int q4 = warp & 3, grp = warp >> 2;
   const int p = q4 * 32 + lane;                 // point (row / TMEM lane)
-  const int cbase = half * (HP / 2);            // this thread's column half
+  const int c0 = grp * 16;                      // this thread's 16 columns
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + pl.o_bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 8);
   const float* s_small = reinterpret_cast<const float*>(sm + pl.o_small);
@@ -452,11 +459,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_load_weights<OP>(pl, a.params, sm);
-  if (half == 0) {  // layer-0 input tile: streams d/dx and d/dy are the constant unit vectors
-    uint32_t ex[8] = {OP::pack(1.f, 0.f), 0, 0, 0, 0, 0, 0, 0};
-    uint32_t ey[8] = {OP::pack(0.f, 1.f), 0, 0, 0, 0, 0, 0, 0};
-    st16(xbuf + 256 * 16, 16, p, 0, ex);
-    st16(xbuf + 512 * 16, 16, p, 0, ey);
+  if (grp == 0) {  // layer-0 input tile: streams d/dx and d/dy are the constant unit vectors
+    uint32_t ex[4] = {OP::pack(1.f, 0.f), 0, 0, 0};
+    uint32_t ey[4] = {OP::pack(0.f, 1.f), 0, 0, 0};
+    uint32_t zz[4] = {0, 0, 0, 0};
+    st8(xbuf + 256 * 16, 16, p, 0, ex);
+    st8(xbuf + 256 * 16, 16, p, 8, zz);
+    st8(xbuf + 512 * 16, 16, p, 0, ey);
+    st8(xbuf + 512 * 16, 16, p, 8, zz);
   }
   fence_proxy_async();
   tc_fence_before();
@@ -468,9 +478,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
   bool failed = false;
   const int L = pl.L;
   uint32_t wfirst = 0xFFFFFFFFu;   // bit i: Wbar_i accumulator not yet written (thread 0)
-  float accL[HP / 2];              // output-layer weight gradient, this thread's columns and points
+  float accL[16];                  // output-layer weight gradient: this thread's columns, its points
 #pragma unroll
-  for (int k = 0; k < HP / 2; ++k) accL[k] = 0.f;
+  for (int k = 0; k < 16; ++k) accL[k] = 0.f;
   int bufH[2] = {-1, -1};
   const float sc = seed_scale(a.seed_absmax);   // adjoint scale (1 for BF16)
   const double inv_sc = 1.0 / (double)sc;
@@ -497,22 +507,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
   // forward epilogue of hidden map i from D into activation tile `ob`
   auto fwd_epilogue_store = [&](int i, uint8_t* ob) {
     const int Nout = pl.WP[i], wo = pl.w[i + 1];
+    if (c0 >= Nout) return;
 #pragma unroll
-    for (int lc = 0; lc < HP / 32; ++lc) {
-      const int c0 = cbase + lc * 16;
-      if (c0 >= Nout) break;
-      float dv[16], dx[16], dy[16];
-      tmem_ld16(tRow + c0, dv);
-      tmem_ld16(tRow + HP + c0, dx);
-      tmem_ld16(tRow + 2 * HP + c0, dy);
+    for (int sc8 = 0; sc8 < 16; sc8 += 8) {
+      const int cc = c0 + sc8;
+      float dv[8], dx[8], dy[8];
+      tmem_ld8(tRow + cc, dv);
+      tmem_ld8(tRow + HP + cc, dx);
+      tmem_ld8(tRow + 2 * HP + cc, dy);
       tmem_wait_ld();
-      uint32_t pv[8], px[8], py[8];
+      uint32_t pv[4], px[4], py[4];
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
+      for (int j = 0; j < 8; j += 2) {
         float tv[2], tx[2], ty[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int o = c0 + j + h;
+          const int o = cc + j + h;
           const float t = tanh_fast(dv[j + h]);
           const float sd = fmaf(-t, t, 1.f);
           tv[h] = o == wo ? 1.f : t;
@@ -523,14 +533,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
         px[j >> 1] = OP::pack(tx[0], tx[1]);
         py[j >> 1] = OP::pack(ty[0], ty[1]);
       }
-      st16(ob, Nout, p, c0, pv);
-      st16(ob + 256 * Nout, Nout, p, c0, px);
-      st16(ob + 512 * Nout, Nout, p, c0, py);
+      st8(ob, Nout, p, cc, pv);
+      st8(ob + 256 * Nout, Nout, p, cc, px);
+      st8(ob + 512 * Nout, Nout, p, cc, py);
     }
   };
   // recompute H_0 .. H_upto into the two activation tiles (H_j -> buf[j & 1])
   auto recompute = [&](int upto, float x, float y) -> bool {
-    layer0_store<HP, OP>(pl, s_small, x, y, p, cbase, sm + pl.o_buf[0]);
+    layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
     publish();
     for (int j = 1; j <= upto; ++j) {
       issue_fwd_map(j);
@@ -552,15 +562,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
     const float su = live ? sc * a.UB[gp] : 0.f;
     const float sx = live ? sc * a.UB[a.P_tot + gp] : 0.f;
     const float sy = live ? sc * a.UB[2 * a.P_tot + gp] : 0.f;
-    if (half == 0) {
-      uint32_t xr[8] = {OP::pack(x, y), OP::pack(1.f, 0.f), 0, 0, 0, 0, 0, 0};
-      st16(xbuf, 16, p, 0, xr);
+    if (grp == 0) {
+      uint32_t xr[4] = {OP::pack(x, y), OP::pack(1.f, 0.f), 0, 0};
+      st8(xbuf, 16, p, 0, xr);
+      uint32_t zz[4] = {0, 0, 0, 0};
+      st8(xbuf, 16, p, 8, zz);
     }
     // ---- forward recompute; the last hidden map's epilogue applies the output
     //      layer and the seeds and writes Zbar_{L-2} (its H is never stored)
     const int last = L - 2;
     if (last >= 1) {
-      layer0_store<HP, OP>(pl, s_small, x, y, p, cbase, sm + pl.o_buf[0]);
+      layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
       publish();
       for (int i = 1; i < last; ++i) {
         issue_fwd_map(i);
@@ -574,52 +586,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
     }
     {
       const int Nout = pl.WP[last], wo = pl.w[last + 1];
+      if (c0 < Nout) {
 #pragma unroll
-      for (int lc = 0; lc < HP / 32; ++lc) {
-        const int c0 = cbase + lc * 16;
-        if (c0 >= Nout) break;
-        float dv[16], dx[16], dy[16];
-        if (last >= 1) {
-          tmem_ld16(tRow + c0, dv);
-          tmem_ld16(tRow + HP + c0, dx);
-          tmem_ld16(tRow + 2 * HP + c0, dy);
-          tmem_wait_ld();
-        } else {      // single hidden layer: pre-activations from layer 0 on CUDA cores
+        for (int sc8 = 0; sc8 < 16; sc8 += 8) {
+          const int cc = c0 + sc8;
+          float dv[8], dx[8], dy[8];
+          if (last >= 1) {
+            tmem_ld8(tRow + cc, dv);
+            tmem_ld8(tRow + HP + cc, dx);
+            tmem_ld8(tRow + 2 * HP + cc, dy);
+            tmem_wait_ld();
+          } else {      // single hidden layer: pre-activations from layer 0 on CUDA cores
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int o = c0 + j;
-            const float wx = s_small[o], wy = s_small[HP + o];
-            dv[j] = fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o]));
-            dx[j] = wx;
-            dy[j] = wy;
+            for (int j = 0; j < 8; ++j) {
+              const int o = cc + j;
+              const float wx = s_small[o], wy = s_small[HP + o];
+              dv[j] = fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o]));
+              dx[j] = wx;
+              dy[j] = wy;
+            }
           }
-        }
-        uint32_t pv[8], px[8], py[8];
+          uint32_t pv[4], px[4], py[4];
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          float zv[2], zx[2], zy[2];
+          for (int j = 0; j < 8; j += 2) {
+            float zv[2], zx[2], zy[2];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int o = c0 + j + h;
-            float t = tanh_fast(dv[j + h]);
-            float sd = fmaf(-t, t, 1.f);
-            float tx = sd * dx[j + h], ty = sd * dy[j + h];
-            if (o == wo) { t = 1.f; tx = 0.f; ty = 0.f; sd = 0.f; }
-            float& acc = accL[lc * 16 + j + h];
-            acc = fmaf(su, t, fmaf(sx, tx, fmaf(sy, ty, acc)));
-            const float wl = s_small[3 * HP + o];
-            const float bv = wl * su, bx = wl * sx, by = wl * sy;
-            zv[h] = sd * bv - 2.f * t * (tx * bx + ty * by);
-            zx[h] = sd * bx;
-            zy[h] = sd * by;
+            for (int h = 0; h < 2; ++h) {
+              const int o = cc + j + h;
+              float t = tanh_fast(dv[j + h]);
+              float sd = fmaf(-t, t, 1.f);
+              float tx = sd * dx[j + h], ty = sd * dy[j + h];
+              if (o == wo) { t = 1.f; tx = 0.f; ty = 0.f; sd = 0.f; }
+              float& acc = accL[sc8 + j + h];
+              acc = fmaf(su, t, fmaf(sx, tx, fmaf(sy, ty, acc)));
+              const float wl = s_small[3 * HP + o];
+              const float bv = wl * su, bx = wl * sx, by = wl * sy;
+              zv[h] = sd * bv - 2.f * t * (tx * bx + ty * by);
+              zx[h] = sd * bx;
+              zy[h] = sd * by;
+            }
+            pv[j >> 1] = OP::pack(zv[0], zv[1]);
+            px[j >> 1] = OP::pack(zx[0], zx[1]);
+            py[j >> 1] = OP::pack(zy[0], zy[1]);
           }
-          pv[j >> 1] = OP::pack(zv[0], zv[1]);
-          px[j >> 1] = OP::pack(zx[0], zx[1]);
-          py[j >> 1] = OP::pack(zy[0], zy[1]);
+          st8(zb, Nout, p, cc, pv);
+          st8(zb + 256 * Nout, Nout, p, cc, px);
+          st8(zb + 512 * Nout, Nout, p, cc, py);
         }
-        st16(zb, Nout, p, c0, pv);
-        st16(zb + 256 * Nout, Nout, p, c0, px);
-        st16(zb + 512 * Nout, Nout, p, c0, py);
       }
     }
     publish();
@@ -653,36 +666,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
         // Zbar_{i-1} from Tbar_{i-1} (tensor memory) and H_{i-1} (shared tile), tanh rule
         const int K = pl.WP[i - 1];
         const uint8_t* hb = sm + pl.o_buf[(i - 1) & 1];
+        if (c0 < K) {
 #pragma unroll
-        for (int lc = 0; lc < HP / 32; ++lc) {
-          const int c0 = cbase + lc * 16;
-          if (c0 >= K) break;
-          float bv[16], bx[16], by[16], hv[16], hx[16], hy[16];
-          tmem_ld16(tRow + c0, bv);
-          tmem_ld16(tRow + HP + c0, bx);
-          tmem_ld16(tRow + 2 * HP + c0, by);
-          ld16<OP>(hb, K, p, c0, hv);
-          ld16<OP>(hb + 256 * K, K, p, c0, hx);
-          ld16<OP>(hb + 512 * K, K, p, c0, hy);
-          tmem_wait_ld();
-          uint32_t pv[8], px[8], py[8];
+          for (int sc8 = 0; sc8 < 16; sc8 += 8) {
+            const int cc = c0 + sc8;
+            float bv[8], bx[8], by[8], hv[8], hx[8], hy[8];
+            tmem_ld8(tRow + cc, bv);
+            tmem_ld8(tRow + HP + cc, bx);
+            tmem_ld8(tRow + 2 * HP + cc, by);
+            ld8<OP>(hb, K, p, cc, hv);
+            ld8<OP>(hb + 256 * K, K, p, cc, hx);
+            ld8<OP>(hb + 512 * K, K, p, cc, hy);
+            tmem_wait_ld();
+            uint32_t pv[4], px[4], py[4];
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            float zv[2], zx[2], zy[2];
+            for (int j = 0; j < 8; j += 2) {
+              float zv[2], zx[2], zy[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float t = hv[j + h], sd = fmaf(-t, t, 1.f);
-              zv[h] = sd * bv[j + h] - 2.f * t * (hx[j + h] * bx[j + h] + hy[j + h] * by[j + h]);
-              zx[h] = sd * bx[j + h];
-              zy[h] = sd * by[j + h];
+              for (int h = 0; h < 2; ++h) {
+                const float t = hv[j + h], sd = fmaf(-t, t, 1.f);
+                zv[h] = sd * bv[j + h] - 2.f * t * (hx[j + h] * bx[j + h] + hy[j + h] * by[j + h]);
+                zx[h] = sd * bx[j + h];
+                zy[h] = sd * by[j + h];
+              }
+              pv[j >> 1] = OP::pack(zv[0], zv[1]);
+              px[j >> 1] = OP::pack(zx[0], zx[1]);
+              py[j >> 1] = OP::pack(zy[0], zy[1]);
             }
-            pv[j >> 1] = OP::pack(zv[0], zv[1]);
-            px[j >> 1] = OP::pack(zx[0], zx[1]);
-            py[j >> 1] = OP::pack(zy[0], zy[1]);
+            st8(zb, K, p, cc, pv);
+            st8(zb + 256 * K, K, p, cc, px);
+            st8(zb + 512 * K, K, p, cc, py);
           }
-          st16(zb, K, p, c0, pv);
-          st16(zb + 256 * K, K, p, c0, px);
-          st16(zb + 512 * K, K, p, c0, py);
         }
         publish();
       } else {
@@ -700,21 +714,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
   const uint32_t never_mask = *s_flags;
   double* g = a.gpart + (size_t)blockIdx.x * pl.n_params;
   if (!failed) {
-    if (half == 0) {
+    if (grp == 0) {
       // hidden maps 0..L-2 from tensor memory (M = 64 layout: row o in lane (o/16)*32 + o%16)
       const int o = q4 * 16 + lane;
       for (int i = 0; i <= L - 2; ++i) {
         const int Kb = i >= 1 ? pl.WP[i - 1] : 16;
         const int in = pl.w[i], out = pl.w[i + 1];
         const bool never = (never_mask >> i) & 1u;
-        for (int c0 = 0; c0 < Kb; c0 += 16) {
-          float v[16];
-          tmem_ld16(tRow + pl.c_wbar[i] + c0, v);
+        for (int cb = 0; cb < Kb; cb += 8) {
+          float v[8];
+          tmem_ld8(tRow + pl.c_wbar[i] + cb, v);
           tmem_wait_ld();
           if (lane < 16 && o < out) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int k = c0 + j;
+            for (int j = 0; j < 8; ++j) {
+              const int k = cb + j;
               const double val = never ? 0.0 : (double)v[j] * inv_sc;
               if (k < in) g[pl.off[i] + o * in + k] = val;
               else if (k == in) g[pl.off[i] + out * in + o] = val;
@@ -724,14 +738,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_bwd_tc(TcArgs a) {
       }
     }
   } else {
-    for (int i = tid; i < pl.n_params; i += kTcThreads) g[i] = 0.0;
+    for (int i = tid; i < pl.n_params; i += NT) g[i] = 0.0;
   }
   // output layer: reduce accL over the CTA's 128 points in fixed order
   tc_fence_before();
   __syncthreads();
   float* scratch = reinterpret_cast<float*>(sm + pl.o_buf[0]);   // [128][HP]
 #pragma unroll
-  for (int k = 0; k < HP / 2; ++k) scratch[p * HP + cbase + k] = accL[k];
+  for (int k = 0; k < 16; ++k) scratch[p * HP + c0 + k] = accL[k];
   __syncthreads();
   if (tid < HP) {
     double sum = 0.0;
@@ -781,7 +795,7 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
     p->o_buf[1] = p->o_buf[0];
     p->o_z = p->o_x = 0;
   }
-  p->o_red = o; o += kTile * 4 * 4;
+  p->o_red = o; o += kTile * (HP / 16) * 3 * 4;
   p->o_bar = o; o += 16;
   p->smem = (o + 127) & ~127;
   int cols = 3 * HP;
@@ -804,10 +818,10 @@ int tc_ctas_per_sm(const TcPlan& p, bool reverse) {
   cudaError_t e;
   if (reverse) {
     cudaFuncSetAttribute(mlp_bwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_bwd_tc<HP, OP>, kTcThreads, p.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_bwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
   } else {
     cudaFuncSetAttribute(mlp_fwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_fwd_tc<HP, OP>, kTcThreads, p.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_fwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
   }
   if (e != cudaSuccess || n < 1) n = 1;
   return std::max(1, std::min(n, 512 / p.tmem_cols));
@@ -825,10 +839,10 @@ int launch_tc(fv_ctx ctx, const TcArgs& a, bool reverse, int grid) {
   cudaError_t e;
   if (reverse) {
     e = cudaFuncSetAttribute(mlp_bwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
-    if (e == cudaSuccess) mlp_bwd_tc<HP, OP><<<grid, kTcThreads, a.pl.smem, ctx->stream>>>(a);
+    if (e == cudaSuccess) mlp_bwd_tc<HP, OP><<<grid, tc_threads<HP>(), a.pl.smem, ctx->stream>>>(a);
   } else {
     e = cudaFuncSetAttribute(mlp_fwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
-    if (e == cudaSuccess) mlp_fwd_tc<HP, OP><<<grid, kTcThreads, a.pl.smem, ctx->stream>>>(a);
+    if (e == cudaSuccess) mlp_fwd_tc<HP, OP><<<grid, tc_threads<HP>(), a.pl.smem, ctx->stream>>>(a);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
