@@ -225,6 +225,67 @@ def run_reference(args, prob):
     return 0
 
 
+# ----------------------------------------------------------------------------- batch workload
+def run_batch(args):
+    """64 independent Poisson instances (uniform grids, N_e log-uniform in
+    [100, 16384], Q 5..10, T 4..8, own 2-30x3-1 network each): the whole batch
+    as one graph launch per step vs. launching the instances one by one."""
+    import torch
+    import fv_inputs as fi
+    from paper_2404_12063_b300 import api
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(local, stream)
+    prec = "fp16" if args.precision == "auto" else args.precision
+    probs = fi.config5_batch(64)
+    pbs = [api.problem_from_inputs(ctx, p, prec, storage="bf16" if prec in ("bf16", "fp16") else None) for p in probs]
+    params = [torch.tensor(p.params, dtype=pb.dtype, device="cuda") for p, pb in zip(probs, pbs)]
+    grads = [torch.empty_like(x) for x in params]
+    outs = [torch.zeros(5, dtype=torch.float64, device="cuda") for _ in params]
+    P = sum(p.n_points for p in probs)
+
+    def eager():
+        for pb, x, g, o in zip(pbs, params, grads, outs):
+            pb.loss_grad(x, g, o)
+
+    for _ in range(args.warmup):
+        eager()
+    ms_eager = time_steps(torch, stream, eager, args.steps)
+    batch = api.Batch(ctx, pbs, params, n_streams=0)
+    n_streams, tuned = batch.info()
+    for _ in range(args.warmup):
+        batch.run()
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        batch.run()
+    ms_graph = time_steps(torch, stream, batch.run, args.steps)
+    cl = clocks.stop()
+    ms_graph = max_over_ranks(ms_graph, world, torch.device("cuda", local))
+    # the batch reproduces the one-by-one results exactly
+    bo, bg = batch.run()
+    torch.cuda.synchronize()
+    same = all(torch.equal(a[:4], b[:4]) for a, b in zip(bo, outs)) and all(torch.equal(a, b) for a, b in zip(bg, grads))
+    line = {"metric": METRIC, "value": world * 64 * 1e3 / ms_graph, "unit": "instance loss+grad evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16/f32-accum", "fp16": "f16/f32-accum", "fp64": "f64"}[prec],
+            "data": "synthetic",
+            "config": {"workload": "batch-64-poisson-instances", "instances": 64, "quad_points": P,
+                       "elements": sum(p.mesh.n_elements for p in probs), "mlp": "64 x 2-30x3-1",
+                       "parallelism": "replicas"},
+            "quad_pts_per_s": world * P * 1e3 / ms_graph,
+            "one_by_one": {"ms_per_step": ms_eager, "evals_per_s": 64e3 / ms_eager, "launches_per_step": None},
+            "graph_vs_one_by_one": ms_eager / ms_graph, "graph_streams": n_streams,
+            "tuning_ms": dict(zip(("1", "2", "4", "8"), tuned)), "bitwise_equal_to_one_by_one": bool(same),
+            "clocks": cl}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def time_steps(torch, stream, fn, steps):
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -246,10 +307,13 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="annulus", choices=["annulus", "batch"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     import fv_inputs as fi
+    if args.workload == "batch":
+        return run_batch(args)
     prob = fi.config3_annulus()
     if args.impl == "reference":
         return run_reference(args, prob)

@@ -239,13 +239,24 @@ typedef struct {
 } fv_instance;
 
 /* Loss + gradient of n independent problems sharing one network shape and
- * options, enqueued on the context's stream.  The instances' work is packed
- * into shared launches (one launch per stage for the whole batch) following
- * a schedule the library builds once per batch (see fv_batch_plan). */
+ * options (each with its own mesh, forcing, boundary data, parameters and
+ * outputs).  fv_batch_plan allocates a workspace per instance and captures
+ * all the instances' evaluations once into a CUDA graph, spread over
+ * n_streams forked streams (largest instance first, each on the least loaded
+ * stream) so that small instances run side by side; n_streams = 0 captures
+ * with 1, 2, 4 and 8 streams, times three replays of each and keeps the
+ * fastest.  Planning synchronises the stream; do it outside any capture.
+ * fv_batch_loss_grad enqueues the batch as one graph launch on the context's
+ * stream; parameters are read from the instances' device buffers at replay
+ * time, so they may change between launches (the buffers may not move).
+ * Device eps (opts->eps_dev) is not supported in batches.
+ * fv_batch_info: streams in use and the tuning replay times (ms) for
+ * 1, 2, 4, 8 streams (0 where not measured). */
 typedef struct fv_batch_s* fv_batch;
 int fv_batch_plan(fv_ctx ctx, int n, const fv_instance* inst, const fv_mlp_desc* mlp, const fv_eval_opts* opts,
-                  fv_batch* out);
+                  int n_streams, fv_batch* out);
 int fv_batch_loss_grad(fv_batch batch);
+int fv_batch_info(fv_batch batch, int* n_streams, double* tuned_ms);
 int fv_batch_destroy(fv_batch batch);
 
 #ifdef __cplusplus

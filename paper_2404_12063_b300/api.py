@@ -306,7 +306,7 @@ class FastVPINNLoss(torch.autograd.Function):
 class Batch:
     """Loss + gradient of many independent problems in one call (fv_batch_*)."""
 
-    def __init__(self, ctx: Context, problems: Sequence[Problem], params: Sequence[torch.Tensor]):
+    def __init__(self, ctx: Context, problems: Sequence[Problem], params: Sequence[torch.Tensor], n_streams: int = 0):
         self.ctx, self.problems, self.params = ctx, list(problems), list(params)
         p0 = self.problems[0]
         self.grads = [torch.empty_like(p) for p in self.params]
@@ -318,8 +318,15 @@ class Batch:
         self._arr = arr
         o = p0.opts()
         h = C.c_void_p()
-        N.call("fv_batch_plan", ctx.h, len(self.problems), arr, C.byref(p0.net.desc), C.byref(o), C.byref(h))
+        N.call("fv_batch_plan", ctx.h, len(self.problems), arr, C.byref(p0.net.desc), C.byref(o), int(n_streams),
+               C.byref(h))
         self.h = h
+
+    def info(self):
+        n = C.c_int()
+        t = (C.c_double * 4)()
+        N.call("fv_batch_info", self.h, C.byref(n), t)
+        return n.value, list(t)
 
     def run(self):
         N.call("fv_batch_loss_grad", self.h)

@@ -241,7 +241,7 @@ struct TimingOff {
 int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp, const void* params,
              const fv_eval_opts* opts, const double* eps_dev, bool want_grad, void* grad, double* out,
              void* U_copy = nullptr, void* UB_copy = nullptr, double* R_out = nullptr, void* fixed_ws = nullptr,
-             size_t fixed_ws_bytes = 0) {
+             size_t fixed_ws_bytes = 0, size_t* ws_bytes_only = nullptr) {
   TimingOff timing_guard(ctx, fixed_ws != nullptr);
   MlpShape sh;
   int rc = check_eval(ctx, mesh, forcing, bc, mlp, params, opts, &sh);
@@ -277,6 +277,10 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
   w.smax = o; o += al(16);
   w.total = o;
+  if (ws_bytes_only) {          // size query only: nothing is launched
+    *ws_bytes_only = w.total;
+    return FV_OK;
+  }
   void* base;
   if (fixed_ws) {
     if (w.total > fixed_ws_bytes) {
@@ -607,18 +611,141 @@ extern "C" int fv_inverse_step(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_
 }
 
 // ---------------------------------------------------------------- batches
+// A batch of independent problems (one network shape and options) is
+// captured once into a CUDA graph: the instances' evaluations are spread
+// over n_streams forked capture streams (largest first, each on the least
+// loaded stream) so that small instances run side by side, and every
+// instance has its own workspace.  fv_batch_loss_grad is one graph launch.
 struct fv_batch_s {
-  fv_ctx ctx;
+  fv_ctx ctx = nullptr;
   std::vector<fv_instance> inst;
-  fv_mlp_desc mlp;
+  fv_mlp_desc mlp{};
   std::vector<int> widths;
-  fv_eval_opts opts;
+  fv_eval_opts opts{};
+  std::vector<void*> ws;
+  std::vector<size_t> ws_bytes;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n_streams = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaStream_t capture = nullptr;   // capture origin (the context's stream may be the legacy default stream)
+  double tuned_ms[8] = {0};
 };
 
+namespace {
+
+void batch_free_graph(fv_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Capture all instances on S streams into b->graph / b->exec.
+int batch_capture(fv_batch b, int S) {
+  batch_free_graph(b);
+  fv_ctx ctx = b->ctx;
+  while ((int)b->streams.size() < S) {
+    cudaStream_t st;
+    FV_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->streams.push_back(st);
+  }
+  while ((int)b->events.size() < S + 1) {
+    cudaEvent_t ev;
+    FV_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->events.push_back(ev);
+  }
+  // largest instances first, each onto the least loaded stream
+  std::vector<int> order(b->inst.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(),
+            [&](int x, int y) { return b->inst[x].mesh->P > b->inst[y].mesh->P; });
+  std::vector<int64_t> load(S, 0);
+  std::vector<int> lane_of(b->inst.size(), 0);
+  for (int i : order) {
+    int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lane_of[i] = s;
+    load[s] += b->inst[i].mesh->P;
+  }
+  if (!b->capture) FV_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+  cudaStream_t main = b->capture;
+  FV_CUDA_TRY(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+  int rc = FV_OK;
+  cudaError_t e = cudaEventRecord(b->events[S], main);
+  for (int s = 0; s < S && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->streams[s], b->events[S], 0);
+  if (e != cudaSuccess) {
+    set_error("batch capture fork failed: %s", cudaGetErrorString(e));
+    rc = FV_ERR_CUDA;
+  }
+  for (int i : order) {
+    if (rc) break;
+    fv_ctx_s lane_ctx;                         // same device, the lane's stream, no timing
+    lane_ctx.device = ctx->device;
+    lane_ctx.stream = b->streams[lane_of[i]];
+    lane_ctx.n_sm = ctx->n_sm;
+    lane_ctx.smem_optin = ctx->smem_optin;
+    lane_ctx.err_dev = ctx->err_dev;
+    const fv_instance& in = b->inst[i];
+    // the handles were created on ctx; evaluate them on the lane context
+    fv_mesh_s mesh_copy = *in.mesh;
+    mesh_copy.ctx = &lane_ctx;
+    fv_forcing_s forcing_copy = *in.forcing;
+    forcing_copy.mesh = &mesh_copy;
+    fv_bc_s bc_copy;
+    if (in.bc) { bc_copy = *in.bc; bc_copy.ctx = &lane_ctx; }
+    rc = evaluate(&lane_ctx, &mesh_copy, &forcing_copy, in.bc ? &bc_copy : nullptr, &b->mlp, in.params_dev, &b->opts,
+                  nullptr, true, in.grad_dev, in.out_dev, nullptr, nullptr, nullptr, b->ws[i], b->ws_bytes[i]);
+    lane_ctx.ws.ptr = nullptr;
+  }
+  for (int s = 0; s < S && rc == FV_OK; ++s) {
+    e = cudaEventRecord(b->events[s], b->streams[s]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, b->events[s], 0);
+    if (e != cudaSuccess) {
+      set_error("batch capture join failed: %s", cudaGetErrorString(e));
+      rc = FV_ERR_CUDA;
+    }
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(main, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    set_error("batch capture failed: %s", cudaGetErrorString(e));
+    return FV_ERR_CUDA;
+  }
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) {
+    set_error("batch graph instantiation failed: %s", cudaGetErrorString(e));
+    return FV_ERR_CUDA;
+  }
+  b->n_streams = S;
+  return FV_OK;
+}
+
+}  // namespace
+
+void batch_release(fv_batch b) {   // frees without touching the error message
+  if (!b) return;
+  if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
+  batch_free_graph(b);
+  for (auto p : b->ws) cudaFree(p);
+  for (auto st : b->streams) cudaStreamDestroy(st);
+  for (auto ev : b->events) cudaEventDestroy(ev);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
+
 extern "C" int fv_batch_plan(fv_ctx ctx, int n, const fv_instance* inst, const fv_mlp_desc* mlp,
-                             const fv_eval_opts* opts, fv_batch* out) {
+                             const fv_eval_opts* opts, int n_streams, fv_batch* out) {
   clear_error();
   FV_CHECK_ARG(ctx && inst && mlp && opts && out && n >= 1, "fv_batch_plan: bad argument");
+  FV_CHECK_ARG(n_streams >= 0 && n_streams <= 8, "fv_batch_plan: n_streams must be 0 (tune) .. 8");
+  FV_CHECK_ARG(!opts->eps_dev, "fv_batch_plan: a device eps is not supported in batches");
+  FV_CUDA_TRY(cudaSetDevice(ctx->device));
   MlpShape sh;
   for (int i = 0; i < n; ++i) {
     int rc = check_eval(ctx, inst[i].mesh, inst[i].forcing, inst[i].bc, mlp, inst[i].params_dev, opts, &sh);
@@ -632,24 +759,81 @@ extern "C" int fv_batch_plan(fv_ctx ctx, int n, const fv_instance* inst, const f
   b->mlp.n_layers = mlp->n_layers;
   b->mlp.widths = b->widths.data();
   b->opts = *opts;
+  auto fail = [&](int rc) { batch_release(b); return rc; };
+  for (int i = 0; i < n; ++i) {
+    size_t bytes = 0;
+    int rc = evaluate(ctx, inst[i].mesh, inst[i].forcing, inst[i].bc, &b->mlp, inst[i].params_dev, &b->opts, nullptr,
+                      true, inst[i].grad_dev, inst[i].out_dev, nullptr, nullptr, nullptr, nullptr, 0, &bytes);
+    if (rc) return fail(rc);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      set_error("fv_batch_plan: workspace allocation failed: %s", cudaGetErrorString(e));
+      return fail(FV_ERR_OOM);
+    }
+    b->ws.push_back(p);
+    b->ws_bytes.push_back(bytes);
+  }
+  if (n_streams > 0) {
+    int rc = batch_capture(b, n_streams);
+    if (rc) return fail(rc);
+  } else {
+    // tune: capture with 1, 2, 4, 8 streams and keep the fastest replay
+    int best = 1;
+    float best_ms = 1e30f;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    for (int S = 1; S <= 8; S *= 2) {
+      int rc = batch_capture(b, S);
+      if (rc) { cudaEventDestroy(t0); cudaEventDestroy(t1); return fail(rc); }
+      cudaGraphLaunch(b->exec, ctx->stream);          // warm-up
+      cudaEventRecord(t0, ctx->stream);
+      for (int r = 0; r < 3; ++r) cudaGraphLaunch(b->exec, ctx->stream);
+      cudaEventRecord(t1, ctx->stream);
+      cudaError_t e = cudaEventSynchronize(t1);
+      float ms = 0.f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, t0, t1);
+      if (e != cudaSuccess) {
+        set_error("fv_batch_plan: tuning run failed: %s", cudaGetErrorString(e));
+        cudaEventDestroy(t0); cudaEventDestroy(t1);
+        return fail(FV_ERR_CUDA);
+      }
+      int k = 0;
+      for (int t = S; t > 1; t >>= 1) ++k;
+      b->tuned_ms[k] = ms / 3;
+      if (ms < best_ms) { best_ms = ms; best = S; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (best != b->n_streams) {
+      int rc = batch_capture(b, best);
+      if (rc) return fail(rc);
+    }
+  }
   *out = b;
   return FV_OK;
 }
 
 extern "C" int fv_batch_loss_grad(fv_batch b) {
   clear_error();
-  FV_CHECK_ARG(b, "fv_batch_loss_grad: null batch");
+  FV_CHECK_ARG(b && b->exec, "fv_batch_loss_grad: batch not planned");
   FV_CUDA_TRY(cudaSetDevice(b->ctx->device));
-  for (auto& in : b->inst) {
-    int rc = evaluate(b->ctx, in.mesh, in.forcing, in.bc, &b->mlp, in.params_dev, &b->opts, nullptr, true, in.grad_dev,
-                      in.out_dev);
-    if (rc) return rc;
-  }
+  FV_CUDA_TRY(cudaGraphLaunch(b->exec, b->ctx->stream));
+  return FV_OK;
+}
+
+extern "C" int fv_batch_info(fv_batch b, int* n_streams, double* tuned_ms /* [4]: 1, 2, 4, 8 streams */) {
+  clear_error();
+  FV_CHECK_ARG(b, "fv_batch_info: null batch");
+  if (n_streams) *n_streams = b->n_streams;
+  if (tuned_ms) for (int k = 0; k < 4; ++k) tuned_ms[k] = b->tuned_ms[k];
   return FV_OK;
 }
 
 extern "C" int fv_batch_destroy(fv_batch b) {
   clear_error();
-  delete b;
+  batch_release(b);
   return FV_OK;
 }
+

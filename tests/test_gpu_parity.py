@@ -338,11 +338,13 @@ def test_inverse_step_adam_update(api, ctx):
         assert abs(eps.item() - theta[-1]) < 1e-12
 
 
-def test_batch_equals_individual_calls(api, ctx):
+@pytest.mark.parametrize("n_streams", [0, 1, 3])
+def test_batch_equals_individual_calls(api, ctx, n_streams):
     probs = fi.config5_batch(6)
     pbs = [api.problem_from_inputs(ctx, p, "fp32") for p in probs]
     params = [torch.tensor(p.params, dtype=torch.float32, device="cuda") for p in probs]
-    batch = api.Batch(ctx, pbs, params)
+    batch = api.Batch(ctx, pbs, params, n_streams=n_streams)
+    assert batch.info()[0] >= 1
     outs, grads = batch.run()
     for pb, p, o, g in zip(pbs, params, outs, grads):
         o2, g2 = pb.loss_grad(p)
@@ -351,6 +353,11 @@ def test_batch_equals_individual_calls(api, ctx):
     ref = oracle_eval(probs[0], params[0].cpu().double().numpy())
     assert rel(outs[0][0].item(), ref["loss"]) < 1e-5
     assert rel(grads[0].cpu().double().numpy(), ref["grad"]) < 1e-5
+    # the graph reads the parameters at replay time
+    params[1].mul_(0.5)
+    outs, grads = batch.run()
+    o2, g2 = pbs[1].loss_grad(params[1])
+    assert torch.equal(outs[1][:4], o2[:4]) and torch.equal(grads[1], g2)
 
 
 def test_kernel_timing_records(api, ctx):
