@@ -84,11 +84,11 @@ def ncu_traffic(kernel, variant):
     return e.get("bytes_per_launch")
 
 
-def contract_bytes(mesh, gsize):
+def contract_bytes(mesh, gsize, fsize=4):
     """Algorithmic bytes of one contraction launch: G once (no padding), F,
     the gradient field in (u_x, u_y) and the seeds out (3 values per point)."""
     G = mesh.n_elements * mesh.n_comp * mesh.Nt * mesh.Nq * gsize
-    F = mesh.n_elements * mesh.Nt * 8
+    F = mesh.n_elements * mesh.Nt * fsize
     return G + F + mesh.n_points * 2 * 4 + mesh.n_points * 3 * 4, G
 
 
@@ -414,7 +414,9 @@ def main():
     # headline: the fastest variant within its stated tolerance
     tol = {"fp32": 1e-5, "tf32": 2e-2, "bf16": 2e-2, "fp16": 2e-2, "fp64": 1e-10}
     ok = [v for v in results if results[v]["err_loss"] < tol[v] and results[v]["err_grad"] < tol[v]]
-    head = min(ok or list(results), key=lambda v: results[v]["ms"])
+    # FP16 is the 16-bit form that reaches the FP32 run's solution error in training (the metric's
+    # "at stated error"); BF16 is as fast but does not (profiles/precision_claim.md)
+    head = "fp16" if "fp16" in ok else min(ok or list(results), key=lambda v: results[v]["ms"])
     r = results[head]
     evals = world * 1e3 / r["ms"]
 
