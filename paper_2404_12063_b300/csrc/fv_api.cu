@@ -379,6 +379,7 @@ extern "C" int fv_ctx_create(fv_ctx* out, int device, void* stream) {
   c->stream = static_cast<cudaStream_t>(stream);
   c->n_sm = prop.multiProcessorCount;
   c->smem_optin = prop.sharedMemPerBlockOptin;
+  c->smem_per_sm = prop.sharedMemPerMultiprocessor;
   cudaError_t e = cudaMalloc(&c->err_dev, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, sizeof(int) * 4);
   if (e != cudaSuccess) {
@@ -685,6 +686,7 @@ int batch_capture(fv_batch b, int S) {
     lane_ctx.stream = b->streams[lane_of[i]];
     lane_ctx.n_sm = ctx->n_sm;
     lane_ctx.smem_optin = ctx->smem_optin;
+    lane_ctx.smem_per_sm = ctx->smem_per_sm;
     lane_ctx.err_dev = ctx->err_dev;
     const fv_instance& in = b->inst[i];
     // the handles were created on ctx; evaluate them on the lane context

@@ -11,10 +11,11 @@
 //
 // G is streamed from HBM exactly once: each CTA pulls element groups into a
 // ring of shared-memory stages with cp.async.bulk (TMA bulk copies completing
-// on an mbarrier), then runs the row pass (residuals; warp-shuffle sums over
-// q) and the column pass (adjoint seeds; one thread per quadrature point) on
-// the same shared tile.
+// on an mbarrier), then runs the row pass (residuals; one row per lane group,
+// vector loads of G and grad u) and the column pass (adjoint seeds; one
+// q-chunk per lane group) on the same shared tile.
 #include <algorithm>
+#include <cmath>
 
 #include "fv_internal.cuh"
 
@@ -82,6 +83,7 @@ struct ContractArgs {
   const double* eps_d;
   double bx, by, rscale;
   int elems_per_stage, n_stages, n_groups;
+  int sh1, sh2, nq_pad;  // staged kernel: log2 of the row-pass and column-pass splits, padded aux row
   double* partials;     // [gridDim][2]
   int* err;
   double* R_out;        // optional [n_e][Nt] element residuals
@@ -113,7 +115,9 @@ template <class R> __device__ __forceinline__ void cp_async_r(R* dst, const R* s
 template <> __device__ __forceinline__ void cp_async_r<float>(float* d, const float* s) { cp_async4(d, s); }
 template <> __device__ __forceinline__ void cp_async_r<double>(double* d, const double* s) { cp_async8(d, s); }
 
-// Per-stage auxiliary data: u_x, u_y of the group's points and its F rows.
+// Per-stage auxiliary data: u_x, u_y of the stage's points (each element's
+// row padded to nq_pad values so that every q-chunk is vector aligned) and
+// its F rows.
 template <class R>
 struct Aux {
   R* ux;
@@ -121,88 +125,77 @@ struct Aux {
   R* F;
 };
 
-constexpr int kPThreads = 512;                      // pipelined kernel: 16 warps
-constexpr int kPWarps = kPThreads / 32;
+constexpr int kCThreads = 128;                      // staged kernel: 4 warps, several CTAs per SM
+constexpr int kCWarps = kCThreads / 32;
 
-// Row step over NR consecutive test rows (j .. j+NR-1) of one element: the
-// lane's q-chunks of each G row are loaded from the stage once and used for
-// both the residual (butterfly all-reduce over the warp) and the adjoint
-// accumulation.
-template <class R, class Gt, int KQ, int NC, int NR>
-__device__ __forceinline__ void row_step(const Gt* __restrict__ tile_k, int j, int Nt, int Nq, int lane,
-                                         const R (&gu)[KQ], const R (&gw)[KQ], R bx, R by, R eps, R rscale,
-                                         const R* __restrict__ Fr, R (&ax)[KQ], R (&ay)[KQ], R (&av)[KQ],
-                                         KahanR<R>& lsum, KahanR<R>& dsum, double* R_out_row) {
-  R vx[NR][KQ], vy[NR][KQ], vv[NR][KQ];
-  R A[NR], B[NR];
-#pragma unroll
-  for (int t = 0; t < NR; ++t) {
-    const Gt* gx = tile_k + (j + t) * Nq;
-    const Gt* gy = gx + Nt * Nq;
-    const Gt* gv = gy + Nt * Nq;
-    A[t] = 0; B[t] = 0;
-#pragma unroll
-    for (int m = 0; m < KQ; ++m) {
-      const int q = lane + 32 * m;
-      const bool in = (KQ == 1 || m < KQ - 1) ? (q < Nq) : (q < Nq);
-      vx[t][m] = in ? (R)gx[q] : (R)0;
-      vy[t][m] = in ? (R)gy[q] : (R)0;
-      A[t] += vx[t][m] * gu[m] + vy[t][m] * gw[m];
-      if (NC == 3) {
-        vv[t][m] = in ? (R)gv[q] : (R)0;
-        B[t] += vv[t][m] * (bx * gu[m] + by * gw[m]);
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int t = 0; t < NR; ++t) {
-      A[t] += __shfl_xor_sync(0xffffffffu, A[t], o);
-      if (NC == 3) B[t] += __shfl_xor_sync(0xffffffffu, B[t], o);
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < NR; ++t) {
-    const R Rv = eps * A[t] + B[t] - Fr[t];
-    const R Rb = rscale * Rv;
-    if (lane == 0) {
-      lsum.add(Rv * Rv);
-      dsum.add(Rb * A[t]);
-      if (R_out_row) R_out_row[t] = (double)Rv;
-    }
-#pragma unroll
-    for (int m = 0; m < KQ; ++m) {
-      ax[m] += Rb * vx[t][m];
-      ay[m] += Rb * vy[t][m];
-      if (NC == 3) av[m] += Rb * vv[t][m];
-    }
-  }
+__host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+
+// Shared-memory layout of the staged kernel (offsets in bytes); host and
+// device evaluate the same function.
+struct StagedLayout {
+  size_t aux_n;            // R values per aux buffer
+  size_t rb, red, bar, stage, total;
+};
+__host__ __device__ inline StagedLayout staged_layout(int Eg, int Nt, int nqp, int S, size_t stage_bytes,
+                                                      size_t rsz) {
+  StagedLayout L;
+  const int ntp = (Nt + 7) & ~7;
+  L.aux_n = (size_t)2 * Eg * nqp + (size_t)Eg * ntp;
+  L.rb = round128(2 * L.aux_n * rsz);                 // two aux buffers at offset 0
+  L.red = L.rb + round128((size_t)Eg * Nt * rsz);     // Rbar of the stage's rows
+  L.bar = L.red + round128(kCWarps * 4 * 8);          // per-warp loss partials
+  L.stage = L.bar + 128;                              // up to 16 stage barriers
+  L.total = L.stage + (size_t)S * stage_bytes;
+  return L;
 }
 
-// KQ = ceil(Nq / 32) quadrature chunks per lane (lane l owns q = l + 32 m);
-// NC = 2 (diffusion only) or 3 (with the convection/mass component).
-template <class R, class Gt, int KQ, int NC>
-__global__ void __launch_bounds__(kPThreads) contract_pipelined(ContractArgs a) {
+// VEC consecutive values read from shared memory as one aligned access.
+template <class T, int VEC>
+struct alignas(sizeof(T) * VEC) VecT {
+  T v[VEC];
+};
+
+template <class R, class T, int VEC>
+__device__ __forceinline__ void lds_vec(const T* p, R (&out)[VEC]) {
+  const VecT<T, VEC> t = *reinterpret_cast<const VecT<T, VEC>*>(p);
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) out[v] = (R)t.v[v];
+}
+
+// One CTA of 128 threads streams element groups through a ring of S shared
+// stages (cp.async.bulk completing on an mbarrier per stage); several CTAs
+// share an SM so that one CTA's copies overlap the others' arithmetic.  Each
+// staged group is read twice from shared memory, never again from HBM:
+//   pass 1 (residuals): a task is (row (e, j), split h of the row's q-chunks);
+//     the 2^sh1 splits of a row sit in adjacent lanes and meet by shuffles.
+//     The task's lanes read whole VEC-wide chunks of G and of grad u.
+//   pass 2 (seeds): a task is (element, q-chunk, split h of the test rows,
+//     taken interleaved j = h, h + H2, ...); the 2^sh2 splits sit in
+//     adjacent lanes and meet by shuffles.
+// Every sum has a fixed order, so results are bitwise reproducible.
+// NC = 2 (diffusion only) or 3 (with the convection/mass component); VEC
+// divides Nq.
+template <class R, class Gt, int NC, int VEC>
+__global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Nt = a.Nt, Nq = a.Nq, Eg = a.elems_per_stage, S = a.n_stages;
+  const int sh1 = a.sh1, sh2 = a.sh2, H1 = 1 << sh1, H2 = 1 << sh2, nqp = a.nq_pad;
+  const int nch = Nq / VEC;
   const size_t stage_bytes = (size_t)Eg * a.g_stride_bytes;
-  unsigned char* stages = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
-  R* aux_base = reinterpret_cast<R*>(full + S);
-  const int aux_n = 2 * Eg * Nq + Eg * Nt;          // R values per aux buffer
+  const StagedLayout L = staged_layout(Eg, Nt, nqp, S, stage_bytes, sizeof(R));
+  R* aux_base = reinterpret_cast<R*>(smem);
+  R* s_rb = reinterpret_cast<R*>(smem + L.rb);
+  double* s_red = reinterpret_cast<double*>(smem + L.red);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar);
+  unsigned char* stages = smem + L.stage;
   auto aux_of = [&](int b) {
     Aux<R> x;
-    x.ux = aux_base + b * aux_n;
-    x.uy = x.ux + Eg * Nq;
-    x.F = x.uy + Eg * Nq;
+    x.ux = aux_base + b * L.aux_n;
+    x.uy = x.ux + Eg * nqp;
+    x.F = x.uy + Eg * nqp;
     return x;
   };
-  // seed partial sums, one slot per (warp, element) segment: slot = warp + element
-  R* s_seg = aux_base + 2 * aux_n;                    // [kPWarps + Eg - 1][3][Nq]
-  const int n_seg = kPWarps + Eg - 1;
-  double* s_red = reinterpret_cast<double*>(s_seg + ((3 * n_seg * Nq + 1) & ~1));   // [kPWarps][4]
 
   const R eps = (R)(a.eps_d ? *a.eps_d : a.eps_h);
   const R bx = (R)a.bx, by = (R)a.by, rscale = (R)a.rscale;
@@ -211,6 +204,7 @@ __global__ void __launch_bounds__(kPThreads) contract_pipelined(ContractArgs a) 
   R* UB = reinterpret_cast<R*>(a.UB);
   const unsigned char* Gb = reinterpret_cast<const unsigned char*>(a.G);
   const int gstride = (int)(a.g_stride_bytes / (int64_t)sizeof(Gt));
+  const int plane = Nt * Nq;                          // values per component of one element
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -236,11 +230,12 @@ __global__ void __launch_bounds__(kPThreads) contract_pipelined(ContractArgs a) 
       const int e0 = grp * Eg;
       const int ne = min(Eg, a.n_e - e0);
       const int64_t p0 = (int64_t)e0 * Nq;
-      for (int i = tid; i < ne * Nq; i += kPThreads) {
-        cp_async_r<R>(x.ux + i, U + a.P_tot + p0 + i);
-        cp_async_r<R>(x.uy + i, U + 2 * a.P_tot + p0 + i);
+      for (int i = tid; i < ne * Nq; i += kCThreads) {
+        const int k = i / Nq, q = i - k * Nq;
+        cp_async_r<R>(x.ux + k * nqp + q, U + a.P_tot + p0 + i);
+        cp_async_r<R>(x.uy + k * nqp + q, U + 2 * a.P_tot + p0 + i);
       }
-      for (int i = tid; i < ne * Nt; i += kPThreads) cp_async_r<R>(x.F + i, Fsrc + (size_t)e0 * Nt + i);
+      for (int i = tid; i < ne * Nt; i += kCThreads) cp_async_r<R>(x.F + i, Fsrc + (size_t)e0 * Nt + i);
     }
     cp_async_commit();
   };
@@ -248,7 +243,10 @@ __global__ void __launch_bounds__(kPThreads) contract_pipelined(ContractArgs a) 
     for (int it = 0; it < S; ++it) issue(it);
   prefetch_aux(0);
 
-  KahanR<R> lsum, dsum;        // lane 0 of each warp
+  // rounds of each pass: uniform over the CTA (whole warps take part in the shuffles)
+  const int n1 = (Eg * Nt * H1 + kCThreads - 1) / kCThreads;
+  const int n2 = (Eg * nch * H2 + kCThreads - 1) / kCThreads;
+  KahanR<R> lsum, dsum;
   for (int it = 0;; ++it) {
     const int grp = blockIdx.x + it * gridDim.x;
     if (grp >= a.n_groups) break;
@@ -273,90 +271,136 @@ __global__ void __launch_bounds__(kPThreads) contract_pipelined(ContractArgs a) 
     }
     const Gt* tile = reinterpret_cast<const Gt*>(stages + s * stage_bytes);
     const Aux<R> x = aux_of(it & 1);
-
-    // each warp takes a contiguous block of the group's (element, test) rows
     const int n_rows = ne * Nt;
-    const int rpw = (n_rows + kPWarps - 1) / kPWarps;
-    const int r0 = warp * rpw, r1 = min(n_rows, r0 + rpw);
-    if (r0 < r1) {
-      int k = r0 / Nt, j = r0 - k * Nt;
-      R gu[KQ], gw[KQ], ax[KQ], ay[KQ], av[KQ];
-      auto load_elem = [&](int kk) {
+
+    // pass 1: residual of every (element, test) row
+    for (int r1 = 0; r1 < n1; ++r1) {
+      const int task = r1 * kCThreads + tid;
+      const int row = task >> sh1, h = task & (H1 - 1);
+      const bool valid = row < n_rows;
+      R Ax = 0, Ay = 0, Bx = 0, By = 0;
+      if (valid) {
+        const int k = row / Nt, j = row - k * Nt;
+        const Gt* gx = tile + (size_t)k * gstride + (size_t)j * Nq;
+        const R* ux = x.ux + k * nqp;
+        const R* uy = x.uy + k * nqp;
+        const int c1 = ((h + 1) * nch) >> sh1;
+        for (int c = (h * nch) >> sh1; c < c1; ++c) {
+          const int q = c * VEC;
+          R vx[VEC], vy[VEC], wx[VEC], wy[VEC];
+          lds_vec<R, Gt, VEC>(gx + q, vx);
+          lds_vec<R, Gt, VEC>(gx + plane + q, vy);
+          lds_vec<R, R, VEC>(ux + q, wx);
+          lds_vec<R, R, VEC>(uy + q, wy);
 #pragma unroll
-        for (int m = 0; m < KQ; ++m) {
-          const int q = lane + 32 * m;
-          gu[m] = q < Nq ? x.ux[kk * Nq + q] : (R)0;
-          gw[m] = q < Nq ? x.uy[kk * Nq + q] : (R)0;
-          ax[m] = ay[m] = av[m] = (R)0;
-        }
-      };
-      auto flush = [&](int kk) {
-        R* seg = s_seg + (warp + kk) * 3 * Nq;
+          for (int v = 0; v < VEC; ++v) {
+            Ax += vx[v] * wx[v];
+            Ay += vy[v] * wy[v];
+          }
+          if (NC == 3) {
+            R vv[VEC];
+            lds_vec<R, Gt, VEC>(gx + 2 * plane + q, vv);
 #pragma unroll
-        for (int m = 0; m < KQ; ++m) {
-          const int q = lane + 32 * m;
-          if (q < Nq) {
-            seg[q] = ax[m];
-            seg[Nq + q] = ay[m];
-            if (NC == 3) seg[2 * Nq + q] = av[m];
+            for (int v = 0; v < VEC; ++v) {
+              Bx += vv[v] * wx[v];
+              By += vv[v] * wy[v];
+            }
           }
         }
-      };
-      load_elem(k);
-      int r = r0;
-      while (r < r1) {
-        if (j == Nt) { flush(k); ++k; j = 0; load_elem(k); }
-        const Gt* tile_k = tile + k * gstride;
-        double* rout = a.R_out ? a.R_out + (size_t)(e0 + k) * Nt + j : nullptr;
-        if (r + 1 < r1 && j + 1 < Nt) {
-          row_step<R, Gt, KQ, NC, 2>(tile_k, j, Nt, Nq, lane, gu, gw, bx, by, eps, rscale, x.F + r, ax, ay, av,
-                                     lsum, dsum, rout);
-          r += 2; j += 2;
-        } else {
-          row_step<R, Gt, KQ, NC, 1>(tile_k, j, Nt, Nq, lane, gu, gw, bx, by, eps, rscale, x.F + r, ax, ay, av,
-                                     lsum, dsum, rout);
-          r += 1; j += 1;
+      }
+      for (int o = 1; o < H1; o <<= 1) {
+        Ax += __shfl_xor_sync(0xffffffffu, Ax, o);
+        Ay += __shfl_xor_sync(0xffffffffu, Ay, o);
+        if (NC == 3) {
+          Bx += __shfl_xor_sync(0xffffffffu, Bx, o);
+          By += __shfl_xor_sync(0xffffffffu, By, o);
         }
       }
-      flush(k);
+      if (valid && h == 0) {
+        const R A = Ax + Ay;
+        const R Rv = eps * A + (NC == 3 ? bx * Bx + by * By : (R)0) - x.F[row];
+        const R Rb = rscale * Rv;
+        s_rb[row] = Rb;
+        lsum.add(Rv * Rv);
+        dsum.add(Rb * A);
+        if (a.R_out) a.R_out[(size_t)e0 * Nt + row] = (double)Rv;
+      }
     }
     __syncthreads();
-    // seeds dL/du = 0, dL/du_x = eps sum Rbar Gx + bx sum Rbar Gv, likewise y;
-    // an element's segments are summed in warp order (deterministic)
-    const int64_t p0 = (int64_t)e0 * Nq;
-    for (int col = tid; col < ne * Nq; col += kPThreads) {
-      const int k = col / Nq, q = col - k * Nq;
-      const int w_lo = (k * Nt) / rpw, w_hi = min(kPWarps - 1, ((k + 1) * Nt - 1) / rpw);
-      R sx = 0, sy = 0, sv = 0;
-      for (int w = w_lo; w <= w_hi; ++w) {
-        const R* seg = s_seg + (w + k) * 3 * Nq + q;
-        sx += seg[0];
-        sy += seg[Nq];
-        if (NC == 3) sv += seg[2 * Nq];
-      }
-      if (UB) {
-        UB[p0 + col] = (R)0;
-        UB[a.P_tot + p0 + col] = eps * sx + bx * sv;
-        UB[2 * a.P_tot + p0 + col] = eps * sy + by * sv;
+    // pass 2: seeds dL/du = 0, dL/du_x = eps sum_j Rbar Gx + bx sum_j Rbar Gv, likewise y
+    if (UB) {
+      for (int r2 = 0; r2 < n2; ++r2) {
+        const int task = r2 * kCThreads + tid;
+        const int h = task & (H2 - 1), cc = task >> sh2;
+        const int k = cc / nch, c = cc - k * nch;
+        const bool valid = k < ne;
+        R sx[VEC], sy[VEC], sv[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) sx[v] = sy[v] = sv[v] = (R)0;
+        if (valid) {
+          const Gt* gx = tile + (size_t)k * gstride + c * VEC;
+          const R* rb = s_rb + k * Nt;
+          for (int j = h; j < Nt; j += H2) {
+            const R r = rb[j];
+            R vx[VEC], vy[VEC];
+            lds_vec<R, Gt, VEC>(gx + (size_t)j * Nq, vx);
+            lds_vec<R, Gt, VEC>(gx + plane + (size_t)j * Nq, vy);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              sx[v] += r * vx[v];
+              sy[v] += r * vy[v];
+            }
+            if (NC == 3) {
+              R vv[VEC];
+              lds_vec<R, Gt, VEC>(gx + 2 * plane + (size_t)j * Nq, vv);
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) sv[v] += r * vv[v];
+            }
+          }
+        }
+        for (int o = 1; o < H2; o <<= 1) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            sx[v] += __shfl_xor_sync(0xffffffffu, sx[v], o);
+            sy[v] += __shfl_xor_sync(0xffffffffu, sy[v], o);
+            if (NC == 3) sv[v] += __shfl_xor_sync(0xffffffffu, sv[v], o);
+          }
+        }
+        if (valid && h == 0) {
+          const int64_t p = (int64_t)(e0 + k) * Nq + c * VEC;
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            UB[p + v] = (R)0;
+            UB[a.P_tot + p + v] = eps * sx[v] + bx * sv[v];
+            UB[2 * a.P_tot + p + v] = eps * sy[v] + by * sv[v];
+          }
+        }
       }
     }
     __syncthreads();
     if (tid == 0) issue(it + S);
   }
   cp_async_wait0();
+  // loss partials: per-thread compensated sums, then a fixed-order tree in FP64
+  double l = (double)lsum.s - (double)lsum.c, d = (double)dsum.s - (double)dsum.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
   if (lane == 0) {
-    s_red[warp * 4 + 0] = (double)lsum.s; s_red[warp * 4 + 1] = -(double)lsum.c;
-    s_red[warp * 4 + 2] = (double)dsum.s; s_red[warp * 4 + 3] = -(double)dsum.c;
+    s_red[warp * 2] = l;
+    s_red[warp * 2 + 1] = d;
   }
   __syncthreads();
   if (tid == 0) {
-    double l = 0.0, d = 0.0;
-    for (int w = 0; w < kPWarps; ++w) {
-      l += s_red[w * 4 + 0] + s_red[w * 4 + 1];
-      d += s_red[w * 4 + 2] + s_red[w * 4 + 3];
+    double ls = 0.0, ds = 0.0;
+    for (int w = 0; w < kCWarps; ++w) {
+      ls += s_red[w * 2];
+      ds += s_red[w * 2 + 1];
     }
-    a.partials[2 * blockIdx.x] = l;
-    a.partials[2 * blockIdx.x + 1] = d;
+    a.partials[2 * blockIdx.x] = ls;
+    a.partials[2 * blockIdx.x + 1] = ds;
   }
 }
 
@@ -431,36 +475,31 @@ __global__ void __launch_bounds__(kThreads) contract_direct(ContractArgs a) {
   }
 }
 
-size_t pipelined_smem(size_t stage_bytes, int S, int Eg, int Nq, int Nt, size_t rsz) {
-  size_t b = S * stage_bytes + S * 8;
-  b += 2 * (size_t)(2 * Eg * Nq + Eg * Nt) * rsz;              // two aux buffers
-  b += (size_t)((3 * (kPWarps + Eg - 1) * Nq + 1) & ~1) * rsz;  // seed segments
-  b += kPWarps * 4 * 8 + 16;
-  return b;
-}
-
-template <class R, class Gt, int KQ, int NC>
-cudaError_t launch_pip(fv_ctx ctx, const ContractArgs& a, int grid, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(contract_pipelined<R, Gt, KQ, NC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) contract_pipelined<R, Gt, KQ, NC><<<grid, kPThreads, smem, ctx->stream>>>(a);
+template <class R, class Gt, int NC, int VEC>
+cudaError_t launch_staged(fv_ctx ctx, const ContractArgs& a, int grid, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(contract_staged<R, Gt, NC, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess) contract_staged<R, Gt, NC, VEC><<<grid, kCThreads, smem, ctx->stream>>>(a);
   return e;
 }
 
 template <class R, class Gt, int NC>
-cudaError_t launch_pip_kq(fv_ctx ctx, const ContractArgs& a, int grid, size_t smem) {
-  const int kq = (a.Nq + 31) / 32;
-  return kq <= 1 ? launch_pip<R, Gt, 1, NC>(ctx, a, grid, smem)
-       : kq == 2 ? launch_pip<R, Gt, 2, NC>(ctx, a, grid, smem)
-       : kq == 3 ? launch_pip<R, Gt, 3, NC>(ctx, a, grid, smem)
-                 : launch_pip<R, Gt, 4, NC>(ctx, a, grid, smem);
+cudaError_t launch_staged_vec(fv_ctx ctx, const ContractArgs& a, int vec, int grid, size_t smem) {
+  switch (vec) {
+    case 8: if constexpr (sizeof(Gt) * 8 <= 16) return launch_staged<R, Gt, NC, 8>(ctx, a, grid, smem); break;
+    case 4: if constexpr (sizeof(Gt) * 4 <= 16) return launch_staged<R, Gt, NC, 4>(ctx, a, grid, smem); break;
+    case 2: return launch_staged<R, Gt, NC, 2>(ctx, a, grid, smem);
+    default: break;
+  }
+  return launch_staged<R, Gt, NC, 1>(ctx, a, grid, smem);
 }
 
 template <class R, class Gt>
-int launch_t(fv_ctx ctx, const ContractArgs& a, bool pipelined, int grid, size_t smem) {
+int launch_t(fv_ctx ctx, const ContractArgs& a, bool staged, int vec, int grid, size_t smem) {
   cudaError_t e;
-  if (pipelined) {
-    e = a.n_comp == 3 ? launch_pip_kq<R, Gt, 3>(ctx, a, grid, smem) : launch_pip_kq<R, Gt, 2>(ctx, a, grid, smem);
+  if (staged) {
+    e = a.n_comp == 3 ? launch_staged_vec<R, Gt, 3>(ctx, a, vec, grid, smem)
+                      : launch_staged_vec<R, Gt, 2>(ctx, a, vec, grid, smem);
   } else {
     e = cudaFuncSetAttribute(contract_direct<R, Gt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) contract_direct<R, Gt><<<grid, kThreads, smem, ctx->stream>>>(a);
@@ -473,59 +512,101 @@ int launch_t(fv_ctx ctx, const ContractArgs& a, bool pipelined, int grid, size_t
   return FV_OK;
 }
 
+// Launch geometry of the contraction.
+struct ContractPlan {
+  bool staged = false;
+  int vec = 1, E = 0, S = 0, sh1 = 0, sh2 = 0, nqp = 0, grid = 0;
+  size_t smem = 0;
+};
+
+size_t g_value_bytes(fv_precision storage) {
+  return storage == FV_FP64 ? 8 : storage == FV_BF16 ? 2 : 4;
+}
+
+// Staged plan: the vector width is the widest shared-memory access (at most
+// 16 bytes of G) whose width divides Nq.  Elements per stage E and the two
+// split factors minimise a per-element cost model counted in CTA-wide vector
+// steps (idle lanes included), preferring E small enough that three or four
+// CTAs share an SM; stages are double-buffered.
+ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec) {
+  ContractPlan P;
+  const size_t rsz = prec == FV_FP64 ? 8 : 4;
+  const size_t gsz = g_value_bytes(m->storage);
+  const size_t gs = m->g_stride_bytes;
+  int vec = 1;
+  for (int v = 8; v >= 2; v >>= 1)
+    if (v * gsz <= 16 && m->Nq % v == 0) { vec = v; break; }
+  const int nch = m->Nq / vec;
+  const int nqp = (m->Nq + 7) & ~7;
+  const int S = 2;
+  double best = 1e300;
+  for (int E = 1; E <= 16 && E <= m->n_e; ++E) {
+    const StagedLayout L = staged_layout(E, m->Nt, nqp, S, E * gs, rsz);
+    if (L.total > ctx->smem_optin || E * gs > (1u << 20) - 16) break;
+    const int C = (int)std::min<size_t>(4, ctx->smem_per_sm / (L.total + 1024));
+    if (C < 1) break;
+    double c1 = 1e300, c2 = 1e300;
+    int s1 = 0, s2 = 0;
+    for (int sh = 0; sh <= 3 && (1 << sh) <= nch; ++sh) {
+      const int H = 1 << sh;
+      const double rounds = std::ceil((double)E * m->Nt * H / kCThreads);
+      const double c = rounds * (std::ceil((double)nch / H) + 2.0 * sh);
+      if (c < c1) { c1 = c; s1 = sh; }
+    }
+    for (int sh = 0; sh <= 4 && (1 << sh) <= m->Nt; ++sh) {
+      const int H = 1 << sh;
+      const double rounds = std::ceil((double)E * nch * H / kCThreads);
+      const double c = rounds * (std::ceil((double)m->Nt / H) + 0.5 * sh * vec);
+      if (c < c2) { c2 = c; s2 = sh; }
+    }
+    const double occ = C >= 3 ? 1.0 : C == 2 ? 1.25 : 1.6;
+    const double cost = (c1 + c2) / E * occ;
+    if (cost < best) {
+      best = cost;
+      P.staged = true; P.vec = vec; P.E = E; P.S = S; P.sh1 = s1; P.sh2 = s2; P.nqp = nqp; P.smem = L.total;
+      P.grid = std::min<int>((m->n_e + E - 1) / E, ctx->n_sm * C);
+    }
+  }
+  if (!P.staged) {        // an element too large to stage: direct kernel
+    P.smem = (size_t)m->Nt * 8 + kWarps * 4 * 8;
+    P.grid = (int)std::min<int64_t>(m->n_e, (int64_t)ctx->n_sm * 8);
+  }
+  return P;
+}
+
 }  // namespace
 
-// Stage geometry: about 96 KB of G per stage (several elements, so that the
-// per-stage barriers are amortised over many rows), 2-4 stages within ~210 KB.
 int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, int* stages, size_t* smem) {
-  const size_t rsz = prec == FV_FP64 ? 8 : 4;
-  const size_t budget = std::min<size_t>(ctx->smem_optin, 220 * 1024);
-  const size_t gs = m->g_stride_bytes;
-  // as many elements per stage as fit with two stages (up to ~96 KB), then add stages while they fit
-  int E = (int)std::min<size_t>(32, std::max<size_t>(1, (96 * 1024 + gs - 1) / gs));
-  while (E > 1 && pipelined_smem(E * gs, 2, E, m->Nq, m->Nt, rsz) > budget) --E;
-  int S = pipelined_smem(E * gs, 2, E, m->Nq, m->Nt, rsz) <= budget ? 2 : 0;
-  while (S >= 2 && S < 4 && pipelined_smem(E * gs, S + 1, E, m->Nq, m->Nt, rsz) <= budget) ++S;
-  if (S < 2 || E * gs > (1u << 20) - 16 || m->Nq > 128) {   // too large to stage / > 4 q-chunks: direct kernel
-    *eg = 0; *stages = 0;
-    *smem = (size_t)m->Nt * 8 + kWarps * 4 * 8;
-    *grid = (int)std::min<int64_t>(m->n_e, (int64_t)ctx->n_sm * 8);
-    return FV_OK;
-  }
-  const size_t sm = pipelined_smem(E * gs, S, E, m->Nq, m->Nt, rsz);
-  const int n_groups = (m->n_e + E - 1) / E;
-  *eg = E; *stages = S; *smem = sm;
-  *grid = std::min<int>(n_groups, ctx->n_sm);
+  const ContractPlan P = plan_contract(ctx, m, prec);
+  *grid = P.grid; *eg = P.E; *stages = P.S; *smem = P.smem;
   return FV_OK;
 }
 
 int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, const void* U, void* UB, double eps,
                     const double* eps_dev, double bx, double by, double rscale, double* partials, int* n_part,
                     double* R_out) {
-  int grid, E, S;
-  size_t smem;
-  contract_grid(ctx, m, pl.prec, &grid, &E, &S, &smem);
+  const ContractPlan P = plan_contract(ctx, m, pl.prec);
   ContractArgs a;
   a.G = m->G; a.g_stride_bytes = (int64_t)m->g_stride_bytes;
   a.n_e = m->n_e; a.Nt = m->Nt; a.Nq = m->Nq; a.n_comp = m->n_comp;
   a.F = f->F; a.Fr = pl.prec == FV_FP64 ? (const void*)f->F : (const void*)f->F32; a.U = U; a.UB = UB; a.P_tot = pl.P_tot;
   a.eps_h = eps; a.eps_d = eps_dev; a.bx = bx; a.by = by; a.rscale = rscale;
-  a.elems_per_stage = E; a.n_stages = S; a.n_groups = E ? (m->n_e + E - 1) / E : m->n_e;
+  a.elems_per_stage = P.E; a.n_stages = P.S; a.n_groups = P.staged ? (m->n_e + P.E - 1) / P.E : m->n_e;
+  a.sh1 = P.sh1; a.sh2 = P.sh2; a.nq_pad = P.nqp;
   a.partials = partials; a.err = ctx->err_dev; a.R_out = R_out;
-  *n_part = grid;
-  const bool pip = E > 0;
+  *n_part = P.grid;
   cudaEvent_t ta;
   time_begin(ctx, K_CONTRACT, &ta);
   int rc;
   if (pl.prec == FV_FP64) {
     if (m->storage != FV_FP64) { set_error("FP64 evaluation needs FP64 G storage"); return FV_ERR_UNSUPPORTED; }
-    rc = launch_t<double, double>(ctx, a, pip, grid, smem);
+    rc = launch_t<double, double>(ctx, a, P.staged, P.vec, P.grid, P.smem);
   } else if (m->storage == FV_FP32) {
-    rc = launch_t<float, float>(ctx, a, pip, grid, smem);
+    rc = launch_t<float, float>(ctx, a, P.staged, P.vec, P.grid, P.smem);
   } else if (m->storage == FV_BF16) {
-    rc = launch_t<float, __nv_bfloat16>(ctx, a, pip, grid, smem);
+    rc = launch_t<float, __nv_bfloat16>(ctx, a, P.staged, P.vec, P.grid, P.smem);
   } else {
-    rc = launch_t<float, double>(ctx, a, pip, grid, smem);
+    rc = launch_t<float, double>(ctx, a, P.staged, P.vec, P.grid, P.smem);
   }
   time_end(ctx, K_CONTRACT, ta);
   return rc;

@@ -71,6 +71,7 @@ struct fv_ctx_s {
   cudaStream_t stream = nullptr;
   int n_sm = 148;
   size_t smem_optin = 227 * 1024;
+  size_t smem_per_sm = 228 * 1024;
   fv::Workspace ws;
   int* err_dev = nullptr;           // device error word (bounded waits, degenerate elements)
   bool timing = false;
