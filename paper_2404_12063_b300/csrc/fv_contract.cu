@@ -16,6 +16,7 @@
 // q-chunk per lane group) on the same shared tile.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "fv_internal.cuh"
 
@@ -162,6 +163,67 @@ __device__ __forceinline__ void lds_vec(const T* p, R (&out)[VEC]) {
   for (int v = 0; v < VEC; ++v) out[v] = (R)t.v[v];
 }
 
+// BF16 -> FP32 is exact: the BF16 bits are the upper half of the FP32 word.
+// Value 2i of a packed run sits in the low half of 32-bit word i.
+template <int VEC>
+__device__ __forceinline__ void lds_bf16(const __nv_bfloat16* p, float (&out)[VEC]) {
+  if constexpr (VEC == 1) {
+    out[0] = __uint_as_float((uint32_t)*reinterpret_cast<const unsigned short*>(p) << 16);
+  } else {
+    constexpr int W = VEC / 2;
+    const VecT<uint32_t, W> t = *reinterpret_cast<const VecT<uint32_t, W>*>(p);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      out[2 * i] = __uint_as_float(t.v[i] << 16);
+      out[2 * i + 1] = __uint_as_float(t.v[i] & 0xffff0000u);
+    }
+  }
+}
+
+// VEC values of G from shared memory, in the evaluation precision R.
+template <class R, class Gt, int VEC>
+__device__ __forceinline__ void gload(const Gt* p, R (&out)[VEC]) {
+  if constexpr (std::is_same<Gt, __nv_bfloat16>::value) lds_bf16<VEC>(p, out);
+  else lds_vec<R, Gt, VEC>(p, out);
+}
+
+// acc[v] += a[v] * b[v], v < VEC.  In FP32 adjacent lanes go through the
+// packed FP32x2 FMA (two independent round-to-nearest FMAs per instruction).
+template <int VEC>
+__device__ __forceinline__ void fma_vec(float (&acc)[VEC], const float (&a)[VEC], const float (&b)[VEC]) {
+  if constexpr (VEC % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < VEC; i += 2) {
+      const float2 r = __ffma2_rn(make_float2(a[i], a[i + 1]), make_float2(b[i], b[i + 1]),
+                                  make_float2(acc[i], acc[i + 1]));
+      acc[i] = r.x;
+      acc[i + 1] = r.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc[i] += a[i] * b[i];
+  }
+}
+template <int VEC>
+__device__ __forceinline__ void fma_vec(double (&acc)[VEC], const double (&a)[VEC], const double (&b)[VEC]) {
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) acc[i] += a[i] * b[i];
+}
+
+// sum of acc[0..VEC) as a pairwise tree
+template <class R, int VEC>
+__device__ __forceinline__ R tree_sum(const R (&acc)[VEC]) {
+  if constexpr (VEC == 1) {
+    return acc[0];
+  } else {
+    R t[VEC / 2 + VEC % 2];
+#pragma unroll
+    for (int i = 0; i < VEC / 2; ++i) t[i] = acc[2 * i] + acc[2 * i + 1];
+    if constexpr (VEC % 2) t[VEC / 2] = acc[VEC - 1];
+    return tree_sum<R, VEC / 2 + VEC % 2>(t);
+  }
+}
+
 // One CTA of 128 threads streams element groups through a ring of S shared
 // stages (cp.async.bulk completing on an mbarrier per stage); several CTAs
 // share an SM so that one CTA's copies overlap the others' arithmetic.  Each
@@ -281,31 +343,34 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
       R Ax = 0, Ay = 0, Bx = 0, By = 0;
       if (valid) {
         const int k = row / Nt, j = row - k * Nt;
-        const Gt* gx = tile + (size_t)k * gstride + (size_t)j * Nq;
-        const R* ux = x.ux + k * nqp;
-        const R* uy = x.uy + k * nqp;
-        const int c1 = ((h + 1) * nch) >> sh1;
-        for (int c = (h * nch) >> sh1; c < c1; ++c) {
-          const int q = c * VEC;
-          R vx[VEC], vy[VEC], wx[VEC], wy[VEC];
-          lds_vec<R, Gt, VEC>(gx + q, vx);
-          lds_vec<R, Gt, VEC>(gx + plane + q, vy);
-          lds_vec<R, R, VEC>(ux + q, wx);
-          lds_vec<R, R, VEC>(uy + q, wy);
+        const int cb = (h * nch) >> sh1, n = (((h + 1) * nch) >> sh1) - cb;
+        const Gt* px = tile + k * gstride + j * Nq + cb * VEC;
+        const R* pu = x.ux + k * nqp + cb * VEC;
+        const R* pw = pu + Eg * nqp;
+        R ax[VEC], ay[VEC], bxa[VEC], bya[VEC];
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            Ax += vx[v] * wx[v];
-            Ay += vy[v] * wy[v];
-          }
+        for (int v = 0; v < VEC; ++v) ax[v] = ay[v] = bxa[v] = bya[v] = (R)0;
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+          R vx[VEC], vy[VEC], wx[VEC], wy[VEC];
+          gload<R, Gt, VEC>(px + i * VEC, vx);
+          gload<R, Gt, VEC>(px + plane + i * VEC, vy);
+          lds_vec<R, R, VEC>(pu + i * VEC, wx);
+          lds_vec<R, R, VEC>(pw + i * VEC, wy);
+          fma_vec<VEC>(ax, vx, wx);
+          fma_vec<VEC>(ay, vy, wy);
           if (NC == 3) {
             R vv[VEC];
-            lds_vec<R, Gt, VEC>(gx + 2 * plane + q, vv);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              Bx += vv[v] * wx[v];
-              By += vv[v] * wy[v];
-            }
+            gload<R, Gt, VEC>(px + 2 * plane + i * VEC, vv);
+            fma_vec<VEC>(bxa, vv, wx);
+            fma_vec<VEC>(bya, vv, wy);
           }
+        }
+        Ax = tree_sum<R, VEC>(ax);
+        Ay = tree_sum<R, VEC>(ay);
+        if (NC == 3) {
+          Bx = tree_sum<R, VEC>(bxa);
+          By = tree_sum<R, VEC>(bya);
         }
       }
       for (int o = 1; o < H1; o <<= 1) {
@@ -338,23 +403,24 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) sx[v] = sy[v] = sv[v] = (R)0;
         if (valid) {
-          const Gt* gx = tile + (size_t)k * gstride + c * VEC;
-          const R* rb = s_rb + k * Nt;
-          for (int j = h; j < Nt; j += H2) {
-            const R r = rb[j];
-            R vx[VEC], vy[VEC];
-            lds_vec<R, Gt, VEC>(gx + (size_t)j * Nq, vx);
-            lds_vec<R, Gt, VEC>(gx + plane + (size_t)j * Nq, vy);
+          const Gt* px = tile + k * gstride + h * Nq + c * VEC;
+          const R* pr = s_rb + k * Nt + h;
+          const int gstep = Nq << sh2;
+          const int n = (Nt - h + H2 - 1) >> sh2;
+#pragma unroll 4
+          for (int i = 0; i < n; ++i) {
+            const R r = pr[i << sh2];
+            R rr[VEC], vx[VEC], vy[VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              sx[v] += r * vx[v];
-              sy[v] += r * vy[v];
-            }
+            for (int v = 0; v < VEC; ++v) rr[v] = r;
+            gload<R, Gt, VEC>(px + i * gstep, vx);
+            gload<R, Gt, VEC>(px + plane + i * gstep, vy);
+            fma_vec<VEC>(sx, rr, vx);
+            fma_vec<VEC>(sy, rr, vy);
             if (NC == 3) {
               R vv[VEC];
-              lds_vec<R, Gt, VEC>(gx + 2 * plane + (size_t)j * Nq, vv);
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) sv[v] += r * vv[v];
+              gload<R, Gt, VEC>(px + 2 * plane + i * gstep, vv);
+              fma_vec<VEC>(sv, rr, vv);
             }
           }
         }
