@@ -228,21 +228,27 @@ __device__ __forceinline__ R tree_sum(const R (&acc)[VEC]) {
 // stages (cp.async.bulk completing on an mbarrier per stage); several CTAs
 // share an SM so that one CTA's copies overlap the others' arithmetic.  Each
 // staged group is read twice from shared memory, never again from HBM:
-//   pass 1 (residuals): a task is (row (e, j), split h of the row's q-chunks);
-//     the 2^sh1 splits of a row sit in adjacent lanes and meet by shuffles.
-//     The task's lanes read whole VEC-wide chunks of G and of grad u.
-//   pass 2 (seeds): a task is (element, q-chunk, split h of the test rows,
-//     taken interleaved j = h, h + H2, ...); the 2^sh2 splits sit in
-//     adjacent lanes and meet by shuffles.
+//   pass 1 (residuals): a task is (row (e, j), split h of the row's
+//     q-chunks).  Lane = h * (32 / H1) + r, so the lanes of one shared-memory
+//     wavefront read consecutive rows at the same chunk (distinct banks when
+//     the row length in chunks is odd; SKEW rotates each lane's chunk order
+//     otherwise).  The H1 splits meet by shuffles.
+//   pass 2 (seeds): a task is (element, q-chunk c, split h of the test rows
+//     taken interleaved j = h, h + H2, ...); the H2 splits sit in adjacent
+//     lanes and meet by shuffles.
 // Every sum has a fixed order, so results are bitwise reproducible.
 // NC = 2 (diffusion only) or 3 (with the convection/mass component); VEC
-// divides Nq.
-template <class R, class Gt, int NC, int VEC>
+// divides Nq.  CNCH, CNT, CSH1, CSH2 fix the chunks per row, the test count
+// and the two split exponents at compile time for common element shapes
+// (0 / -1: taken from the arguments).
+template <class R, class Gt, int NC, int VEC, bool SKEW, int CNCH = 0, int CNT = 0, int CSH1 = -1, int CSH2 = -1>
 __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int Nt = a.Nt, Nq = a.Nq, Eg = a.elems_per_stage, S = a.n_stages;
-  const int sh1 = a.sh1, sh2 = a.sh2, H1 = 1 << sh1, H2 = 1 << sh2, nqp = a.nq_pad;
+  const int Nt = CNT ? CNT : a.Nt, Nq = CNCH ? CNCH * VEC : a.Nq, Eg = a.elems_per_stage, S = a.n_stages;
+  const int sh1 = CSH1 >= 0 ? CSH1 : a.sh1, sh2 = CSH2 >= 0 ? CSH2 : a.sh2, H1 = 1 << sh1, H2 = 1 << sh2;
+  const int nqp = CNCH ? ((CNCH * VEC + 7) & ~7) : a.nq_pad;
+  const int lg_rpw = 5 - sh1;                         // rows per warp and round: 32 / H1
   const int nch = Nq / VEC;
   const size_t stage_bytes = (size_t)Eg * a.g_stride_bytes;
   const StagedLayout L = staged_layout(Eg, Nt, nqp, S, stage_bytes, sizeof(R));
@@ -337,8 +343,8 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
 
     // pass 1: residual of every (element, test) row
     for (int r1 = 0; r1 < n1; ++r1) {
-      const int task = r1 * kCThreads + tid;
-      const int row = task >> sh1, h = task & (H1 - 1);
+      const int row = ((r1 * kCWarps + warp) << lg_rpw) + (lane & ((1 << lg_rpw) - 1));
+      const int h = lane >> lg_rpw;
       const bool valid = row < n_rows;
       R Ax = 0, Ay = 0, Bx = 0, By = 0;
       if (valid) {
@@ -350,21 +356,24 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
         R ax[VEC], ay[VEC], bxa[VEC], bya[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) ax[v] = ay[v] = bxa[v] = bya[v] = (R)0;
+        int c = SKEW ? row % n : 0;
 #pragma unroll 4
         for (int i = 0; i < n; ++i) {
+          const int o = SKEW ? c * VEC : i * VEC;
           R vx[VEC], vy[VEC], wx[VEC], wy[VEC];
-          gload<R, Gt, VEC>(px + i * VEC, vx);
-          gload<R, Gt, VEC>(px + plane + i * VEC, vy);
-          lds_vec<R, R, VEC>(pu + i * VEC, wx);
-          lds_vec<R, R, VEC>(pw + i * VEC, wy);
+          gload<R, Gt, VEC>(px + o, vx);
+          gload<R, Gt, VEC>(px + plane + o, vy);
+          lds_vec<R, R, VEC>(pu + o, wx);
+          lds_vec<R, R, VEC>(pw + o, wy);
           fma_vec<VEC>(ax, vx, wx);
           fma_vec<VEC>(ay, vy, wy);
           if (NC == 3) {
             R vv[VEC];
-            gload<R, Gt, VEC>(px + 2 * plane + i * VEC, vv);
+            gload<R, Gt, VEC>(px + 2 * plane + o, vv);
             fma_vec<VEC>(bxa, vv, wx);
             fma_vec<VEC>(bya, vv, wy);
           }
+          if (SKEW) c = c + 1 == n ? 0 : c + 1;
         }
         Ax = tree_sum<R, VEC>(ax);
         Ay = tree_sum<R, VEC>(ay);
@@ -373,7 +382,7 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
           By = tree_sum<R, VEC>(bya);
         }
       }
-      for (int o = 1; o < H1; o <<= 1) {
+      for (int o = 16; o >= (1 << lg_rpw); o >>= 1) {
         Ax += __shfl_xor_sync(0xffffffffu, Ax, o);
         Ay += __shfl_xor_sync(0xffffffffu, Ay, o);
         if (NC == 3) {
@@ -541,31 +550,43 @@ __global__ void __launch_bounds__(kThreads) contract_direct(ContractArgs a) {
   }
 }
 
-template <class R, class Gt, int NC, int VEC>
-cudaError_t launch_staged(fv_ctx ctx, const ContractArgs& a, int grid, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(contract_staged<R, Gt, NC, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e == cudaSuccess) contract_staged<R, Gt, NC, VEC><<<grid, kCThreads, smem, ctx->stream>>>(a);
+template <class R, class Gt, int NC, int VEC, bool SKEW, int... Shape>
+cudaError_t launch_staged1(fv_ctx ctx, const ContractArgs& a, int grid, size_t smem) {
+  auto kern = contract_staged<R, Gt, NC, VEC, SKEW, Shape...>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) kern<<<grid, kCThreads, smem, ctx->stream>>>(a);
   return e;
 }
 
+// Compile-time element shapes: (chunks per row, tests, split exponents) of
+// the Q = 10, T = 8 element with 4-wide chunks, as the planner splits it.
+template <class R, class Gt, int NC, int VEC>
+cudaError_t launch_staged(fv_ctx ctx, const ContractArgs& a, bool skew, int grid, size_t smem) {
+  if (skew) return launch_staged1<R, Gt, NC, VEC, true>(ctx, a, grid, smem);
+  if constexpr (VEC == 4 && NC == 2) {
+    if (a.Nq == 100 && a.Nt == 64 && a.sh1 == 1 && a.sh2 == 2)
+      return launch_staged1<R, Gt, NC, VEC, false, 25, 64, 1, 2>(ctx, a, grid, smem);
+  }
+  return launch_staged1<R, Gt, NC, VEC, false>(ctx, a, grid, smem);
+}
+
 template <class R, class Gt, int NC>
-cudaError_t launch_staged_vec(fv_ctx ctx, const ContractArgs& a, int vec, int grid, size_t smem) {
+cudaError_t launch_staged_vec(fv_ctx ctx, const ContractArgs& a, int vec, bool skew, int grid, size_t smem) {
   switch (vec) {
-    case 8: if constexpr (sizeof(Gt) * 8 <= 16) return launch_staged<R, Gt, NC, 8>(ctx, a, grid, smem); break;
-    case 4: if constexpr (sizeof(Gt) * 4 <= 16) return launch_staged<R, Gt, NC, 4>(ctx, a, grid, smem); break;
-    case 2: return launch_staged<R, Gt, NC, 2>(ctx, a, grid, smem);
+    case 8: if constexpr (sizeof(Gt) * 8 <= 16) return launch_staged<R, Gt, NC, 8>(ctx, a, skew, grid, smem); break;
+    case 4: if constexpr (sizeof(Gt) * 4 <= 16) return launch_staged<R, Gt, NC, 4>(ctx, a, skew, grid, smem); break;
+    case 2: return launch_staged<R, Gt, NC, 2>(ctx, a, skew, grid, smem);
     default: break;
   }
-  return launch_staged<R, Gt, NC, 1>(ctx, a, grid, smem);
+  return launch_staged<R, Gt, NC, 1>(ctx, a, skew, grid, smem);
 }
 
 template <class R, class Gt>
-int launch_t(fv_ctx ctx, const ContractArgs& a, bool staged, int vec, int grid, size_t smem) {
+int launch_t(fv_ctx ctx, const ContractArgs& a, bool staged, int vec, bool skew, int grid, size_t smem) {
   cudaError_t e;
   if (staged) {
-    e = a.n_comp == 3 ? launch_staged_vec<R, Gt, 3>(ctx, a, vec, grid, smem)
-                      : launch_staged_vec<R, Gt, 2>(ctx, a, vec, grid, smem);
+    e = a.n_comp == 3 ? launch_staged_vec<R, Gt, 3>(ctx, a, vec, skew, grid, smem)
+                      : launch_staged_vec<R, Gt, 2>(ctx, a, vec, skew, grid, smem);
   } else {
     e = cudaFuncSetAttribute(contract_direct<R, Gt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) contract_direct<R, Gt><<<grid, kThreads, smem, ctx->stream>>>(a);
@@ -580,7 +601,7 @@ int launch_t(fv_ctx ctx, const ContractArgs& a, bool staged, int vec, int grid, 
 
 // Launch geometry of the contraction.
 struct ContractPlan {
-  bool staged = false;
+  bool staged = false, skew = false;
   int vec = 1, E = 0, S = 0, sh1 = 0, sh2 = 0, nqp = 0, grid = 0;
   size_t smem = 0;
 };
@@ -589,11 +610,15 @@ size_t g_value_bytes(fv_precision storage) {
   return storage == FV_FP64 ? 8 : storage == FV_BF16 ? 2 : 4;
 }
 
+int gcd_int(int a, int b) { return b ? gcd_int(b, a % b) : a; }
+
 // Staged plan: the vector width is the widest shared-memory access (at most
 // 16 bytes of G) whose width divides Nq.  Elements per stage E and the two
 // split factors minimise a per-element cost model counted in CTA-wide vector
-// steps (idle lanes included), preferring E small enough that three or four
-// CTAs share an SM; stages are double-buffered.
+// steps (idle lanes included), preferring E small enough that four CTAs
+// share an SM; stages are double-buffered.  The row pass rotates each lane's
+// chunk order when the row length in chunks shares a factor with the number
+// of lanes that one shared-memory wavefront serves.
 ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec) {
   ContractPlan P;
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
@@ -604,6 +629,7 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec) {
     if (v * gsz <= 16 && m->Nq % v == 0) { vec = v; break; }
   const int nch = m->Nq / vec;
   const int nqp = (m->Nq + 7) & ~7;
+  const int wave_lanes = (int)std::min<size_t>(32, std::max<size_t>(1, 128 / (vec * gsz)));
   const int S = 2;
   double best = 1e300;
   for (int E = 1; E <= 16 && E <= m->n_e; ++E) {
@@ -625,11 +651,12 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec) {
       const double c = rounds * (std::ceil((double)m->Nt / H) + 0.5 * sh * vec);
       if (c < c2) { c2 = c; s2 = sh; }
     }
-    const double occ = C >= 3 ? 1.0 : C == 2 ? 1.25 : 1.6;
+    const double occ = C >= 4 ? 1.0 : C == 3 ? 1.1 : C == 2 ? 1.3 : 2.0;
     const double cost = (c1 + c2) / E * occ;
     if (cost < best) {
       best = cost;
       P.staged = true; P.vec = vec; P.E = E; P.S = S; P.sh1 = s1; P.sh2 = s2; P.nqp = nqp; P.smem = L.total;
+      P.skew = gcd_int(nch, wave_lanes) > 1;
       P.grid = std::min<int>((m->n_e + E - 1) / E, ctx->n_sm * C);
     }
   }
@@ -666,13 +693,13 @@ int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, con
   int rc;
   if (pl.prec == FV_FP64) {
     if (m->storage != FV_FP64) { set_error("FP64 evaluation needs FP64 G storage"); return FV_ERR_UNSUPPORTED; }
-    rc = launch_t<double, double>(ctx, a, P.staged, P.vec, P.grid, P.smem);
+    rc = launch_t<double, double>(ctx, a, P.staged, P.vec, P.skew, P.grid, P.smem);
   } else if (m->storage == FV_FP32) {
-    rc = launch_t<float, float>(ctx, a, P.staged, P.vec, P.grid, P.smem);
+    rc = launch_t<float, float>(ctx, a, P.staged, P.vec, P.skew, P.grid, P.smem);
   } else if (m->storage == FV_BF16) {
-    rc = launch_t<float, __nv_bfloat16>(ctx, a, P.staged, P.vec, P.grid, P.smem);
+    rc = launch_t<float, __nv_bfloat16>(ctx, a, P.staged, P.vec, P.skew, P.grid, P.smem);
   } else {
-    rc = launch_t<float, double>(ctx, a, P.staged, P.vec, P.grid, P.smem);
+    rc = launch_t<float, double>(ctx, a, P.staged, P.vec, P.skew, P.grid, P.smem);
   }
   time_end(ctx, K_CONTRACT, ta);
   return rc;
