@@ -241,6 +241,8 @@ def run_batch(args):
     prec = "fp16" if args.precision == "auto" else args.precision
     probs = fi.config5_batch(64)
     pbs = [api.problem_from_inputs(ctx, p, prec, storage="bf16" if prec in ("bf16", "fp16") else None) for p in probs]
+    for pb in pbs:                      # contraction launch plan per mesh (setup, not timed)
+        pb.mesh.autotune(prec)
     params = [torch.tensor(p.params, dtype=pb.dtype, device="cuda") for p, pb in zip(probs, pbs)]
     grads = [torch.empty_like(x) for x in params]
     outs = [torch.zeros(5, dtype=torch.float64, device="cuda") for _ in params]
@@ -351,6 +353,8 @@ def main():
         torch.cuda.synchronize()
         meshes[st + "_ms"] = ev0.elapsed_time(ev1)
     build_wall = time.perf_counter() - t0
+    # contraction launch plan per mesh (fv_autotune; setup, not timed)
+    tuned = {st: meshes[st].autotune("fp32") for st in ("fp32", "bf16")}
 
     hbm, bf16_peak, bf16_sus, sm_max, peak_kind = peaks()
     fwd_fl, bwd_fl = mlp_flops_per_point(prob.widths)
@@ -485,6 +489,7 @@ def main():
         "quad_pts_per_s": world * prob.n_points * 1e3 / r["ms"],
         "variants": variants_out,
         "g_build_ms": {"fp32": meshes["fp32_ms"], "bf16": meshes["bf16_ms"]},
+        "contract_autotune_ms": {st: {"two_stage": round(a, 5), "one_stage": round(b, 5)} for st, (a, b) in tuned.items()},
         "clocks": r["clocks"],
         "e2e": {"value": world * 1e3 / r["ms_e2e"], "unit": UNIT, "h2d_bytes_per_step": r["bytes_h2d"],
                 "d2h_bytes_per_step": r["bytes_d2h"]},

@@ -139,6 +139,19 @@ int fv_mesh_quad_points(fv_mesh mesh, double* xy_host);
 int fv_mesh_copy_g(fv_mesh mesh, double* g_host);
 int fv_mesh_destroy(fv_mesh mesh);
 
+/* Autotune the contraction of Alg. 3 for this mesh at evaluation precision
+ * `mlp_precision`: times each candidate launch plan (one or two shared-memory
+ * stages per CTA, with the element grouping and lane splits the planner picks
+ * for each) on zero-valued inputs and keeps the fastest in the mesh handle.
+ * Later evaluations with this mesh and precision use it; without a call the
+ * two-stage plan is used.  Plans differ only in how sums are grouped, so a
+ * tuned and an untuned evaluation agree to rounding, and each plan is
+ * deterministic.  ms_out (nullable, host, 2 doubles) receives the median
+ * times of the two-stage and one-stage plans.
+ * Errors: FV_ERR_ARG (null mesh, precision not 0..4), FV_ERR_OOM, FV_ERR_CUDA.
+ * Synchronises the stream; not allowed during stream capture. */
+int fv_autotune(fv_ctx ctx, fv_mesh mesh, fv_precision mlp_precision, double* ms_out);
+
 /* F[e][j] = sum_q Gv[e][j][q] f(X[e][q]) (App. A.2, "Compute Forcing Matrix"),
  * assembled in FP64 from the caller's f at the quadrature points
  * (host [n_elements*Q*Q], the order of fv_mesh_quad_points). */

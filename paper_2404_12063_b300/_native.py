@@ -59,6 +59,7 @@ SIGNATURES = {
     "fv_mesh_quad_points": [_vp, _dp],
     "fv_mesh_copy_g": [_vp, _dp],
     "fv_mesh_destroy": [_vp],
+    "fv_autotune": [_vp, _vp, C.c_int, _dp],
     "fv_assemble_forcing": [_vp, _dp, _pvp],
     "fv_forcing_copy": [_vp, _dp],
     "fv_forcing_destroy": [_vp],

@@ -103,6 +103,14 @@ class Mesh:
         N.call("fv_mesh_copy_g", self.h, out.ctypes.data)
         return out
 
+    def autotune(self, precision="fp32") -> tuple:
+        """Time the contraction's launch plans for this mesh at `precision`
+        and keep the fastest (fv_autotune).  Returns the median milliseconds
+        of the two-stage and one-stage plans."""
+        ms = (C.c_double * 2)()
+        N.call("fv_autotune", self.ctx.h, self.h, _prec(precision), ms)
+        return ms[0], ms[1]
+
     def close(self):
         if getattr(self, "h", None):
             N.lib().fv_mesh_destroy(self.h)

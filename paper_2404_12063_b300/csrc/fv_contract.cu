@@ -616,10 +616,11 @@ int gcd_int(int a, int b) { return b ? gcd_int(b, a % b) : a; }
 // 16 bytes of G) whose width divides Nq.  Elements per stage E and the two
 // split factors minimise a per-element cost model counted in CTA-wide vector
 // steps (idle lanes included), preferring E small enough that four CTAs
-// share an SM; stages are double-buffered.  The row pass rotates each lane's
+// share an SM.  Stages per CTA: double-buffered by default; one stage with up
+// to eight CTAs per SM where autotuning found that faster for the mesh.  The row pass rotates each lane's
 // chunk order when the row length in chunks shares a factor with the number
 // of lanes that one shared-memory wavefront serves.
-ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec) {
+ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages = 0) {
   ContractPlan P;
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
   const size_t gsz = g_value_bytes(m->storage);
@@ -630,12 +631,14 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec) {
   const int nch = m->Nq / vec;
   const int nqp = (m->Nq + 7) & ~7;
   const int wave_lanes = (int)std::min<size_t>(32, std::max<size_t>(1, 128 / (vec * gsz)));
-  const int S = 2;
+  const int tuned = m->contract_stages[prec == FV_FP64 ? 1 : 0];
+  const int S = stages ? stages : tuned ? tuned : 2;
+  const size_t max_ctas = S == 1 ? 8 : 4;
   double best = 1e300;
   for (int E = 1; E <= 16 && E <= m->n_e; ++E) {
     const StagedLayout L = staged_layout(E, m->Nt, nqp, S, E * gs, rsz);
     if (L.total > ctx->smem_optin || E * gs > (1u << 20) - 16) break;
-    const int C = (int)std::min<size_t>(4, ctx->smem_per_sm / (L.total + 1024));
+    const int C = (int)std::min<size_t>(max_ctas, ctx->smem_per_sm / (L.total + 1024));
     if (C < 1) break;
     double c1 = 1e300, c2 = 1e300;
     int s1 = 0, s2 = 0;
@@ -673,6 +676,76 @@ int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, 
   const ContractPlan P = plan_contract(ctx, m, prec);
   *grid = P.grid; *eg = P.E; *stages = P.S; *smem = P.smem;
   return FV_OK;
+}
+
+// Times the one- and two-stage plans on zero-valued inputs (median of seven
+// launches after two warm-up launches each) and keeps the faster one.
+int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) {
+  const int slot = prec == FV_FP64 ? 1 : 0;
+  const size_t rsz = prec == FV_FP64 ? 8 : 4;
+  const ContractPlan p2 = plan_contract(ctx, m, prec, 2), p1 = plan_contract(ctx, m, prec, 1);
+  if (ms_out) ms_out[0] = ms_out[1] = 0.0;
+  if (!p2.staged || !p1.staged) return FV_OK;      // direct kernel: nothing to choose
+  EvalPlan pl;
+  pl.prec = prec;
+  pl.P_mesh = pl.P_tot = m->P;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t u_bytes = 3 * (size_t)m->P * rsz, nf = (size_t)m->n_e * m->Nt;
+  const size_t o_ub = al(u_bytes), o_f = o_ub + al(u_bytes), o_f32 = o_f + al(nf * 8), o_part = o_f32 + al(nf * 4);
+  const size_t total = o_part + al((size_t)std::max(p1.grid, p2.grid) * 16);
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, total) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("autotune: cannot allocate %zu bytes of scratch", total);
+    return FV_ERR_OOM;
+  }
+  fv_forcing_s fz;
+  fz.mesh = m;
+  fz.F = reinterpret_cast<double*>(buf + o_f);
+  fz.F32 = reinterpret_cast<float*>(buf + o_f32);
+  double* part = reinterpret_cast<double*>(buf + o_part);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = FV_OK;
+  auto fail = [&](cudaError_t e) {
+    set_error("autotune: %s", cudaGetErrorString(e));
+    rc = FV_ERR_CUDA;
+  };
+  cudaError_t ce = cudaMemsetAsync(buf, 0, total, ctx->stream);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) fail(ce);
+  const int saved = m->contract_stages[slot];
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  double med[2] = {0.0, 0.0};
+  for (int pass = 0; pass < 2 && rc == FV_OK; ++pass) {
+    m->contract_stages[slot] = pass == 0 ? 2 : 1;
+    float t[7] = {0};
+    int n_part = 0;
+    for (int r = 0; r < 9 && rc == FV_OK; ++r) {
+      if (r >= 2 && (ce = cudaEventRecord(e0, ctx->stream)) != cudaSuccess) { fail(ce); break; }
+      rc = launch_contract(ctx, m, &fz, pl, buf, buf + o_ub, 1.0, nullptr, 0.0, 0.0, 1.0, part, &n_part, nullptr);
+      if (rc || r < 2) continue;
+      if ((ce = cudaEventRecord(e1, ctx->stream)) != cudaSuccess || (ce = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (ce = cudaEventElapsedTime(&t[r - 2], e0, e1)) != cudaSuccess)
+        fail(ce);
+    }
+    if (rc == FV_OK) {
+      std::sort(t, t + 7);
+      med[pass] = t[3];
+    }
+  }
+  ctx->timing = timing;
+  if (rc == FV_OK && (ce = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) fail(ce);
+  m->contract_stages[slot] = rc == FV_OK ? (med[1] < med[0] ? 1 : 2) : saved;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (ms_out && rc == FV_OK) {
+    ms_out[0] = med[0];
+    ms_out[1] = med[1];
+  }
+  return rc;
 }
 
 int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, const void* U, void* UB, double eps,

@@ -94,6 +94,7 @@ struct fv_mesh_s {
   double* verts = nullptr;          // [n_v][2]
   int* cells = nullptr;             // [n_e][4]
   int n_v = 0;
+  int contract_stages[2] = {0, 0};  // tuned stages per CTA (FP32 / FP64 evaluation); 0 = default
 };
 
 struct fv_forcing_s {
@@ -174,6 +175,7 @@ struct EvalPlan {
 
 int launch_mlp_fwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
                    void* U);
+int autotune_contract(fv_ctx ctx, fv_mesh mesh, fv_precision prec, double* ms_out);
 int launch_contract(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U, void* UB,
                     double eps, const double* eps_dev, double bx, double by, double rscale, double* partials,
                     int* n_partials_out, double* R_out = nullptr);

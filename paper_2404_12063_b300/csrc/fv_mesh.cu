@@ -328,6 +328,14 @@ extern "C" int fv_mesh_destroy(fv_mesh m) {
   return FV_OK;
 }
 
+extern "C" int fv_autotune(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) {
+  clear_error();
+  FV_CHECK_ARG(ctx && m, "fv_autotune: null context or mesh");
+  FV_CHECK_ARG(prec >= FV_FP64 && prec <= FV_FP16, "fv_autotune: precision %d out of range", (int)prec);
+  FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  return autotune_contract(ctx, m, prec, ms_out);
+}
+
 extern "C" int fv_assemble_forcing(fv_mesh m, const double* f, fv_forcing* out) {
   clear_error();
   FV_CHECK_ARG(m && f && out, "fv_assemble_forcing: null argument");

@@ -290,6 +290,25 @@ def test_deterministic(api, ctx):
     assert torch.equal(o1, o2) and torch.equal(g1, g2)
 
 
+@pytest.mark.parametrize("k", [2, 4])
+def test_autotuned_contraction_matches_oracle(api, ctx, k):
+    """fv_autotune picks the one- or two-stage contraction plan for the mesh;
+    the tuned evaluation still matches the oracle and is reproducible."""
+    prob = cfg(k)
+    pb = api.problem_from_inputs(ctx, prob, "fp32")
+    ms2, ms1 = pb.mesh.autotune("fp32")
+    assert ms2 > 0 and ms1 > 0
+    params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+    o1, g1 = pb.loss_grad(params)
+    o1, g1 = o1.clone(), g1.clone()
+    o2, g2 = pb.loss_grad(params)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2) and torch.equal(g1, g2)
+    ref = oracle_eval(prob, params.cpu().double().numpy())
+    assert rel(o1[0].item(), ref["loss"]) < TOL["fp32"]
+    assert rel(g1.cpu().double().numpy(), ref["grad"]) < TOL["fp32"]
+
+
 # ---------------------------------------------------------------- bindings, Adam, batches
 def test_autograd_function(api, ctx):
     prob = cfg(1)
