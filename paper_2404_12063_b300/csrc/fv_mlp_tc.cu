@@ -269,39 +269,55 @@ __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_sm
   }
 }
 
+// MMAs into one accumulator run as a dependent chain; MMAs into independent
+// accumulators overlap in the tensor pipe.  So the three streams' MMAs are
+// issued round-robin (K step outer, stream inner), and the reverse step
+// interleaves its adjoint-product MMAs into the weight-gradient chain.
+
 // Forward MMAs of map i: D_s (columns s*HP) = H_{i-1,s} W_i^T, K = Kin, N = Nout.
 __device__ __forceinline__ void issue_fwd(uint32_t fmt, uint32_t tD, uint32_t abuf, uint32_t wbuf, int Kin, int Nout,
                                           int HP) {
   const uint32_t id = idesc_f16(fmt, 128, Nout, 0, 0);
-  for (int s = 0; s < 3; ++s)
-    for (int kk = 0; kk < Kin / 16; ++kk) {
+  for (int kk = 0; kk < Kin / 16; ++kk)
+    for (int s = 0; s < 3; ++s) {
       const uint64_t ad = sdesc(abuf + s * 256 * Kin + kk * 256, 128, Kin * 16);
       const uint64_t bd = sdesc(wbuf + kk * 256, 128, Kin * 16);
       mma_bf16(tD + s * HP, ad, bd, id, kk > 0);
     }
 }
 
-// Tbar_s (columns s*HP) = Zbar_s W_i: A = Zbar (K-major, K = Nout), B = W_i read MN-major (N = Kin).
-__device__ __forceinline__ void issue_tbar(uint32_t fmt, uint32_t tD, uint32_t zbuf, uint32_t wbuf, int Kin, int Nout,
-                                           int HP) {
-  const uint32_t id = idesc_f16(fmt, 128, Kin, 0, 1);
-  for (int s = 0; s < 3; ++s)
-    for (int kk = 0; kk < Nout / 16; ++kk) {
-      const uint64_t ad = sdesc(zbuf + s * 256 * Nout + kk * 256, 128, Nout * 16);
-      const uint64_t bd = sdesc(wbuf + kk * 2 * Kin * 16, Kin * 16, 128);
-      mma_bf16(tD + s * HP, ad, bd, id, kk > 0);
+// Reverse step of map i >= 1 (all weight-gradient MMAs, then all adjoint
+// products: mixing the two shapes in the issue order slows the pipe):
+//   Wbar_i (M = 64 rows o, N = Kin) += sum over streams and points of Zbar^T B,
+//     both read MN-major; K runs over 3 streams x 128 points (one chain);
+//   Tbar_s (columns s*HP) = Zbar_s W_i: A = Zbar (K-major, K = Nout), B = W_i
+//     read MN-major (N = Kin), streams round-robin.
+__device__ __forceinline__ void issue_reverse(uint32_t fmt, uint32_t tD, uint32_t tW, uint32_t zbuf, uint32_t wbuf,
+                                              uint32_t bbuf, int Kin, int Nout, int HP, bool first) {
+  const uint32_t idw = idesc_f16(fmt, 64, Kin, 1, 1);
+  for (int w = 0; w < 3 * (kTile / 16); ++w) {
+    const int s = w / (kTile / 16), ps = w % (kTile / 16);
+    const uint64_t ad = sdesc(zbuf + s * 256 * Nout + ps * 2 * Nout * 16, Nout * 16, 128);
+    const uint64_t bd = sdesc(bbuf + s * 256 * Kin + ps * 2 * Kin * 16, Kin * 16, 128);
+    mma_bf16(tW, ad, bd, idw, (first && w == 0) ? 0u : 1u);
+  }
+  const uint32_t idt = idesc_f16(fmt, 128, Kin, 0, 1);
+  for (int kk = 0; kk < Nout / 16; ++kk)
+    for (int s = 0; s < 3; ++s) {
+      const uint64_t at = sdesc(zbuf + s * 256 * Nout + kk * 256, 128, Nout * 16);
+      const uint64_t bt = sdesc(wbuf + kk * 2 * Kin * 16, Kin * 16, 128);
+      mma_bf16(tD + s * HP, at, bt, idt, kk > 0);
     }
 }
 
-// Wbar (M = 64 rows o, N = Nb) += sum over streams and points of Zbar^T B,
-// both read MN-major; K runs over 3 streams x 128 points.
-__device__ __forceinline__ void issue_wbar(uint32_t fmt, uint32_t tW, uint32_t zbuf, int Kz, uint32_t bbuf, int Kb,
-                                           bool first) {
-  const uint32_t id = idesc_f16(fmt, 64, Kb, 1, 1);
+// Reverse step of map 0 (inputs x, y, 1 in a 16-column tile): Wbar_0, one chain.
+__device__ __forceinline__ void issue_wbar0(uint32_t fmt, uint32_t tW, uint32_t zbuf, int Kz, uint32_t xbuf,
+                                            bool first) {
+  const uint32_t id = idesc_f16(fmt, 64, 16, 1, 1);
   for (int s = 0; s < 3; ++s)
     for (int ps = 0; ps < kTile / 16; ++ps) {
       const uint64_t ad = sdesc(zbuf + s * 256 * Kz + ps * 2 * Kz * 16, Kz * 16, 128);
-      const uint64_t bd = sdesc(bbuf + s * 256 * Kb + ps * 2 * Kb * 16, Kb * 16, 128);
+      const uint64_t bd = sdesc(xbuf + s * 256 * 16 + ps * 2 * 16 * 16, 16 * 16, 128);
       mma_bf16(tW, ad, bd, id, (first && s == 0 && ps == 0) ? 0u : 1u);
     }
 }
@@ -553,15 +569,21 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 1) mlp_bwd_tc(TcArgs a) {
     return true;
   };
 
-  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+  // this thread's point inputs for a tile: coordinates and (scaled) seeds
+  auto fetch = [&](int64_t tile, float (&in)[5]) {
     const int64_t gp = tile * kTile + p;
-    float x, y;
-    point_xy(a, gp, x, y);
+    point_xy(a, gp, in[0], in[1]);
     const bool live = gp < a.P_tot;
-    const float su = live ? sc * a.UB[gp] : 0.f;
-    const float sx = live ? sc * a.UB[a.P_tot + gp] : 0.f;
-    const float sy = live ? sc * a.UB[2 * a.P_tot + gp] : 0.f;
+    in[2] = live ? sc * a.UB[gp] : 0.f;
+    in[3] = live ? sc * a.UB[a.P_tot + gp] : 0.f;
+    in[4] = live ? sc * a.UB[2 * a.P_tot + gp] : 0.f;
+  };
+  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
+  float nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (blockIdx.x < n_tiles) fetch(blockIdx.x, nxt);
+  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+    const float x = nxt[0], y = nxt[1], su = nxt[2], sx = nxt[3], sy = nxt[4];
+    if (tile + gridDim.x < n_tiles) fetch(tile + gridDim.x, nxt);     // next tile's inputs, in flight meanwhile
     if (grp == 0) {
       uint32_t xr[4] = {OP::pack(x, y), OP::pack(1.f, 0.f), 0, 0};
       st8(xbuf, 16, p, 0, xr);
@@ -656,9 +678,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 1) mlp_bwd_tc(TcArgs a) {
       }
       if (tid == 0) {
         tc_fence_after();
-        issue_wbar(OP::fmt, tD + pl.c_wbar[i], su32(zb), pl.WP[i], bsrc, Kb, (wfirst >> i) & 1u);
+        if (i >= 1)
+          issue_reverse(OP::fmt, tD, tD + pl.c_wbar[i], su32(zb), su32(sm + pl.o_w[i]), bsrc, pl.WP[i - 1], pl.WP[i],
+                        HP, (wfirst >> i) & 1u);
+        else
+          issue_wbar0(OP::fmt, tD + pl.c_wbar[0], su32(zb), pl.WP[0], bsrc, (wfirst >> 0) & 1u);
         wfirst &= ~(1u << i);
-        if (i >= 1) issue_tbar(OP::fmt, tD, su32(zb), su32(sm + pl.o_w[i]), pl.WP[i - 1], pl.WP[i], HP);
         mma_commit(bar);
       }
       if (!sync_mma()) { failed = true; break; }
@@ -725,6 +750,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 1) mlp_bwd_tc(TcArgs a) {
           float v[8];
           tmem_ld8(tRow + pl.c_wbar[i] + cb, v);
           tmem_wait_ld();
+
           if (lane < 16 && o < out) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
