@@ -139,6 +139,20 @@ int fv_mesh_quad_points(fv_mesh mesh, double* xy_host);
 int fv_mesh_copy_g(fv_mesh mesh, double* g_host);
 int fv_mesh_destroy(fv_mesh mesh);
 
+/* How evaluations with this mesh contract grad u against the premultipliers.
+ * FV_G_STORED (default): stream the stored G tensor (Alg. 3, G precomputed as
+ * in App. A.2).  FV_G_MATRIX_FREE: rebuild the premultipliers inside the
+ * contraction from the element vertices and the reference tables and sum them
+ * by sum factorisation over the tensor-product test functions; the stored G
+ * is not read.  Both give the same loss, residuals and gradients up to
+ * rounding (the matrix-free form rounds geometry in the evaluation precision
+ * instead of rounding G to the storage precision).  The paper precomputes G
+ * (Sec. 4.2); the matrix-free form is this library's extension.
+ * Errors: FV_ERR_ARG (null mesh, mode not 0 or 1). */
+#define FV_G_STORED 0
+#define FV_G_MATRIX_FREE 1
+int fv_mesh_set_g_mode(fv_mesh mesh, int mode);
+
 /* Autotune the contraction of Alg. 3 for this mesh at evaluation precision
  * `mlp_precision`: times each candidate launch plan (one or two shared-memory
  * stages per CTA, with the element grouping and lane splits the planner picks

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfastvpinn.so")
 
 FV_OK, FV_ERR_ARG, FV_ERR_DEGENERATE_ELEMENT, FV_ERR_UNSUPPORTED, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_TIMEOUT = range(7)
 FV_FP64, FV_FP32, FV_TF32, FV_BF16, FV_FP16 = range(5)
+FV_G_STORED, FV_G_MATRIX_FREE = 0, 1
 FV_NORM_TEST, FV_NORM_ELEM = range(2)
 
 ERR_NAMES = {1: "FV_ERR_ARG", 2: "FV_ERR_DEGENERATE_ELEMENT", 3: "FV_ERR_UNSUPPORTED", 4: "FV_ERR_OOM",
@@ -60,6 +61,7 @@ SIGNATURES = {
     "fv_mesh_copy_g": [_vp, _dp],
     "fv_mesh_destroy": [_vp],
     "fv_autotune": [_vp, _vp, C.c_int, _dp],
+    "fv_mesh_set_g_mode": [_vp, C.c_int],
     "fv_assemble_forcing": [_vp, _dp, _pvp],
     "fv_forcing_copy": [_vp, _dp],
     "fv_forcing_destroy": [_vp],

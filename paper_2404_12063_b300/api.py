@@ -103,6 +103,13 @@ class Mesh:
         N.call("fv_mesh_copy_g", self.h, out.ctypes.data)
         return out
 
+    def set_g_mode(self, mode: str = "stored"):
+        """'stored' streams the stored G tensor; 'matrix_free' rebuilds it in
+        the contraction from the element vertices (fv_mesh_set_g_mode)."""
+        m = {"stored": N.FV_G_STORED, "matrix_free": N.FV_G_MATRIX_FREE}[mode]
+        N.call("fv_mesh_set_g_mode", self.h, m)
+        self.g_mode = mode
+
     def autotune(self, precision="fp32") -> tuple:
         """Time the contraction's launch plans for this mesh at `precision`
         and keep the fastest (fv_autotune).  Returns the median milliseconds
@@ -353,16 +360,19 @@ class Batch:
 
 
 def problem_from_inputs(ctx: Context, prob, precision="fp32", storage=None, norm="test", with_bc=True,
-                        mesh: Optional[Mesh] = None) -> Problem:
+                        mesh: Optional[Mesh] = None, g_mode: Optional[str] = None) -> Problem:
     """Build the library handles for a problem description with fields mesh
     (vertices, cells), quad_order, test_order, widths, f(x, y), bd_xy, bd_g,
-    tau, sensor_xy, sensor_u, gamma, eps, b (duck-typed)."""
+    tau, sensor_xy, sensor_u, gamma, eps, b (duck-typed).  g_mode
+    ('stored' / 'matrix_free') sets the mesh's contraction mode."""
     prec = _prec(precision)
     if storage is None:
         storage = "fp64" if prec == N.FV_FP64 else "fp32"
     with_mass = prob.b[0] != 0.0 or prob.b[1] != 0.0
     if mesh is None:
         mesh = Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, prob.quad_order, prob.test_order, storage, with_mass)
+    if g_mode is not None:
+        mesh.set_g_mode(g_mode)
     X = mesh.quad_points()
     forcing = Forcing(mesh, prob.f(X[:, 0], X[:, 1]))
     bc = None

@@ -90,18 +90,6 @@ struct ContractArgs {
   double* R_out;        // optional [n_e][Nt] element residuals
 };
 
-// Compensated (Kahan) accumulator in the evaluation precision.
-template <class R>
-struct KahanR {
-  R s = 0, c = 0;
-  __device__ __forceinline__ void add(R x) {
-    const R y = x - c;
-    const R t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -673,6 +661,12 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
 }  // namespace
 
 int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, int* stages, size_t* smem) {
+  if (m->g_mode == FV_G_MATRIX_FREE) {
+    int wpb;
+    mfree_grid(ctx, m, prec, grid, &wpb, smem);
+    *eg = 0; *stages = 0;
+    return FV_OK;
+  }
   const ContractPlan P = plan_contract(ctx, m, prec);
   *grid = P.grid; *eg = P.E; *stages = P.S; *smem = P.smem;
   return FV_OK;
@@ -685,7 +679,7 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
   const ContractPlan p2 = plan_contract(ctx, m, prec, 2), p1 = plan_contract(ctx, m, prec, 1);
   if (ms_out) ms_out[0] = ms_out[1] = 0.0;
-  if (!p2.staged || !p1.staged) return FV_OK;      // direct kernel: nothing to choose
+  if (!p2.staged || !p1.staged || m->g_mode != FV_G_STORED) return FV_OK;   // nothing to choose
   EvalPlan pl;
   pl.prec = prec;
   pl.P_mesh = pl.P_tot = m->P;
@@ -751,6 +745,8 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
 int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, const void* U, void* UB, double eps,
                     const double* eps_dev, double bx, double by, double rscale, double* partials, int* n_part,
                     double* R_out) {
+  if (m->g_mode == FV_G_MATRIX_FREE)
+    return launch_contract_mfree(ctx, m, f, pl, U, UB, eps, eps_dev, bx, by, rscale, partials, n_part, R_out);
   const ContractPlan P = plan_contract(ctx, m, pl.prec);
   ContractArgs a;
   a.G = m->G; a.g_stride_bytes = (int64_t)m->g_stride_bytes;

@@ -95,6 +95,7 @@ struct fv_mesh_s {
   int* cells = nullptr;             // [n_e][4]
   int n_v = 0;
   int contract_stages[2] = {0, 0};  // tuned stages per CTA (FP32 / FP64 evaluation); 0 = default
+  int g_mode = FV_G_STORED;         // contraction from the stored G or matrix-free
 };
 
 struct fv_forcing_s {
@@ -162,6 +163,39 @@ struct KSum {
   __device__ __forceinline__ double value() const { return s + c; }
 };
 
+// Bilinear map of a quad element (App. A.1): x = x0 + x1 xi + x2 eta + x3 xi eta
+// (likewise y) from its counter-clockwise vertices b0..b3.
+struct Bilin { double x0, x1, x2, x3, y0, y1, y2, y3; };
+
+__device__ __forceinline__ Bilin bilin_coeffs(const double* verts, const int* cell) {
+  double vx[4], vy[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { vx[k] = verts[2 * cell[k]]; vy[k] = verts[2 * cell[k] + 1]; }
+  Bilin c;
+  c.x0 = 0.25 * (vx[0] + vx[1] + vx[2] + vx[3]);
+  c.x1 = 0.25 * (-vx[0] + vx[1] + vx[2] - vx[3]);
+  c.x2 = 0.25 * (-vx[0] - vx[1] + vx[2] + vx[3]);
+  c.x3 = 0.25 * (vx[0] - vx[1] + vx[2] - vx[3]);
+  c.y0 = 0.25 * (vy[0] + vy[1] + vy[2] + vy[3]);
+  c.y1 = 0.25 * (-vy[0] + vy[1] + vy[2] - vy[3]);
+  c.y2 = 0.25 * (-vy[0] - vy[1] + vy[2] + vy[3]);
+  c.y3 = 0.25 * (vy[0] - vy[1] + vy[2] - vy[3]);
+  return c;
+}
+
+
+// Compensated (Kahan) accumulator in the evaluation precision.
+template <class R>
+struct KahanR {
+  R s = 0, c = 0;
+  __device__ __forceinline__ void add(R x) {
+    const R y = x - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
 // ------------------------------------------------------------------ launchers
 // Each returns FV_OK or an error code and enqueues on ctx->stream.
 struct EvalPlan {
@@ -176,6 +210,10 @@ struct EvalPlan {
 int launch_mlp_fwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
                    void* U);
 int autotune_contract(fv_ctx ctx, fv_mesh mesh, fv_precision prec, double* ms_out);
+int launch_contract_mfree(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U,
+                          void* UB, double eps, const double* eps_dev, double bx, double by, double rscale,
+                          double* partials, int* n_partials_out, double* R_out);
+void mfree_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* warps_per_cta, size_t* smem);
 int launch_contract(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U, void* UB,
                     double eps, const double* eps_dev, double bx, double by, double rscale, double* partials,
                     int* n_partials_out, double* R_out = nullptr);

@@ -75,24 +75,6 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_g<__nv_bfloat16>(double
   return __float2bfloat16_rn((float)v);
 }
 
-struct Bilin { double x0, x1, x2, x3, y0, y1, y2, y3; };
-
-__device__ __forceinline__ Bilin bilin_coeffs(const double* verts, const int* cell) {
-  double vx[4], vy[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) { vx[k] = verts[2 * cell[k]]; vy[k] = verts[2 * cell[k] + 1]; }
-  Bilin c;
-  c.x0 = 0.25 * (vx[0] + vx[1] + vx[2] + vx[3]);
-  c.x1 = 0.25 * (-vx[0] + vx[1] + vx[2] - vx[3]);
-  c.x2 = 0.25 * (-vx[0] - vx[1] + vx[2] + vx[3]);
-  c.x3 = 0.25 * (vx[0] - vx[1] + vx[2] - vx[3]);
-  c.y0 = 0.25 * (vy[0] + vy[1] + vy[2] + vy[3]);
-  c.y1 = 0.25 * (-vy[0] + vy[1] + vy[2] - vy[3]);
-  c.y2 = 0.25 * (-vy[0] - vy[1] + vy[2] + vy[3]);
-  c.y3 = 0.25 * (vy[0] - vy[1] + vy[2] - vy[3]);
-  return c;
-}
-
 // One CTA per element (grid-stride).  FP64 throughout; the adjugate form
 // w (y_eta v_xi - y_xi v_eta) = w |J| dv/dx needs no division by |J|.
 template <class Gt>
@@ -325,6 +307,14 @@ extern "C" int fv_mesh_destroy(fv_mesh m) {
   if (!m) return FV_OK;
   cudaFree(m->G); cudaFree(m->X); cudaFree(m->tables); cudaFree(m->verts); cudaFree(m->cells);
   delete m;
+  return FV_OK;
+}
+
+extern "C" int fv_mesh_set_g_mode(fv_mesh m, int mode) {
+  clear_error();
+  FV_CHECK_ARG(m, "fv_mesh_set_g_mode: null mesh");
+  FV_CHECK_ARG(mode == FV_G_STORED || mode == FV_G_MATRIX_FREE, "fv_mesh_set_g_mode: mode %d is not 0 or 1", mode);
+  m->g_mode = mode;
   return FV_OK;
 }
 

@@ -54,8 +54,8 @@ def _with(prob, **kw):
     return fi.Problem(**d)
 
 
-def gpu_eval(api, ctx, prob, precision, storage=None, norm="test", intermediates=False):
-    pb = api.problem_from_inputs(ctx, prob, precision, storage, norm)
+def gpu_eval(api, ctx, prob, precision, storage=None, norm="test", intermediates=False, g_mode=None):
+    pb = api.problem_from_inputs(ctx, prob, precision, storage, norm, g_mode=g_mode)
     params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
     if intermediates:
         out, U, UB, R = pb.intermediates(params)
@@ -70,10 +70,10 @@ def oracle_eval(prob, params64, norm=0, **kw):
     return oracle.Bound(prob, norm=norm).loss_grad(params64, n_threads=NTH, **kw)
 
 
-def check_against_oracle(api, ctx, prob, precision, storage=None, norm="test", tol=None, tol_lv=None):
+def check_against_oracle(api, ctx, prob, precision, storage=None, norm="test", tol=None, tol_lv=None, g_mode=None):
     tol = TOL[precision] if tol is None else tol
     tol_lv = tol if tol_lv is None else tol_lv
-    pb, params, out, grad = gpu_eval(api, ctx, prob, precision, storage, norm)
+    pb, params, out, grad = gpu_eval(api, ctx, prob, precision, storage, norm, g_mode=g_mode)
     p64 = params.cpu().double().numpy()          # the oracle sees the same (rounded) parameters
     ref = oracle_eval(prob, p64, 0 if norm == "test" else 1)
     assert rel(out[0], ref["loss"]) < tol, (out[0], ref["loss"])
@@ -307,6 +307,53 @@ def test_autotuned_contraction_matches_oracle(api, ctx, k):
     ref = oracle_eval(prob, params.cpu().double().numpy())
     assert rel(o1[0].item(), ref["loss"]) < TOL["fp32"]
     assert rel(g1.cpu().double().numpy(), ref["grad"]) < TOL["fp32"]
+
+
+# ---------------------------------------------------------------- matrix-free contraction
+@pytest.mark.parametrize("k,precision", [(1, "fp64"), (1, "fp32"), (2, "fp64"), (2, "fp32"), (3, "fp32"), (4, "fp64"),
+                                         (4, "fp32")])
+def test_matrix_free_matches_oracle(api, ctx, k, precision):
+    check_against_oracle(api, ctx, cfg(k), precision, g_mode="matrix_free")
+
+
+@pytest.mark.parametrize("ne,Q,T", [(1, 2, 1), (3, 3, 2), (17, 13, 9), (2, 32, 16), (37, 7, 3)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_matrix_free_ragged_sizes(api, ctx, ne, Q, T, precision):
+    base = fi.rect_grid(ne, 1, 0.0, 1.0, 0.0, 0.3)
+    mesh = fi.jitter_nodes(base, ~fi.boundary_nodes_of(base), 0.2, seed=ne)
+    u, f = fi.sinsin(3.0)
+    widths = [2, 7, 5, 1] if ne % 2 else [2, 13, 1]
+    bd = fi.square_boundary_points(3, 0, 1, 0, 0.3)
+    prob = fi.Problem("ragged", mesh, Q, T, widths, fi.random_bias_params(widths, ne, 1), u, f, bd,
+                      u(bd[:, 0], bd[:, 1]), eps=0.9, b=(0.4, 0.2), tau=2.0)
+    check_against_oracle(api, ctx, prob, precision, g_mode="matrix_free")
+
+
+def test_matrix_free_intermediates_elementwise(api, ctx):
+    """Residuals R[e][j] and seeds dL/du_x, dL/du_y of the matrix-free
+    contraction against the oracle, element by element, with convection."""
+    prob = _with(cfg(1), b=(0.2, -0.3), eps=0.7, params=fi.random_bias_params(cfg(1).widths, 1, 1))
+    pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp64", intermediates=True, g_mode="matrix_free")
+    ref = oracle_eval(prob, prob.params, want_R=True, want_ubar=True)
+    P = prob.n_points
+    assert np.max(np.abs(R - ref["R"])) < 1e-11 * np.max(np.abs(ref["R"]))
+    ub = ref["ubar"].reshape(-1, 2)
+    assert np.max(np.abs(UB[1, :P] - ub[:, 0])) < 1e-11 * np.max(np.abs(ub))
+    assert np.max(np.abs(UB[2, :P] - ub[:, 1])) < 1e-11 * np.max(np.abs(ub))
+    assert np.all(UB[0, :P] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_matrix_free_tensor_core(api, ctx, precision):
+    check_against_oracle(api, ctx, cfg(3), precision, g_mode="matrix_free")
+
+
+def test_matrix_free_mode_argument_errors(api, ctx):
+    from paper_2404_12063_b300 import FVError, _native as N
+    pb = api.problem_from_inputs(ctx, cfg(1), "fp64")
+    with pytest.raises(FVError) as ei:
+        N.call("fv_mesh_set_g_mode", pb.mesh.h, 7)
+    assert ei.value.code == N.FV_ERR_ARG
 
 
 # ---------------------------------------------------------------- bindings, Adam, batches
