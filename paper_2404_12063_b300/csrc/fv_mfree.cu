@@ -20,6 +20,18 @@
 namespace fv {
 namespace {
 
+__device__ __forceinline__ void cp_async_val(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_val(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 struct MfArgs {
   const double* verts;
   const int* cells;
@@ -36,10 +48,12 @@ struct MfArgs {
   double* R_out;            // optional [n_e][T*T]
 };
 
+// One element's inputs staged in shared memory: u_x, u_y at its nodes and its F row.
+__host__ __device__ inline int mf_stage_values(int Q, int T) { return ((2 * Q * Q + T * T) + 1) & ~1; }
 // Shared memory per warp (values of R): P, Qm(, C) over the Q x Q nodes, the
-// half-contracted T x Q arrays T1, T2(, T3), and the Rbar rows.
+// half-contracted T x Q arrays T1, T2(, T3), the Rbar rows and two input stages.
 __host__ __device__ inline int mf_warp_values(int Q, int T, int nc) {
-  return (nc == 3 ? 3 : 2) * (Q * Q + T * Q) + T * T;
+  return (nc == 3 ? 3 : 2) * (Q * Q + T * Q) + T * T + 2 * mf_stage_values(Q, T);
 }
 __host__ __device__ inline int mf_table_values(int Q, int T) { return 2 * Q + 2 * T * Q; }
 
@@ -61,6 +75,8 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   R* T2 = T1 + TQ;
   R* T3 = T2 + TQ;                             // NC == 3
   R* Rb = T1 + (NC == 3 ? 3 : 2) * TQ;
+  R* stage = Rb + Nt;                          // [2][u_x (Nq), u_y (Nq), F (Nt)]
+  const int SV = mf_stage_values(Q, T);
 
   const R eps = (R)(a.eps_d ? *a.eps_d : a.eps_h);
   const R bx = (R)a.bx, by = (R)a.by, rscale = (R)a.rscale;
@@ -69,17 +85,47 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   const R* F = reinterpret_cast<const R*>(a.Fr);
   KahanR<R> lsum, dsum;
 
-  for (int e = blockIdx.x * nw + warp; e < a.n_e; e += gridDim.x * nw) {
-    const Bilin cb = bilin_coeffs(a.verts, a.cells + 4 * (size_t)e);
-    const R x1 = (R)cb.x1, x2 = (R)cb.x2, x3 = (R)cb.x3, y1 = (R)cb.y1, y2 = (R)cb.y2, y3 = (R)cb.y3;
+  // the element's u_x, u_y and F rows go to a stage with cp.async, one element ahead
+  auto fetch = [&](int e, R* st) {
+    if (e < a.n_e) {
+      const int64_t p0 = (int64_t)e * Nq;
+      for (int q = lane; q < Nq; q += 32) {
+        cp_async_val(st + q, U + a.P_tot + p0 + q);
+        cp_async_val(st + Nq + q, U + 2 * a.P_tot + p0 + q);
+      }
+      for (int j = lane; j < Nt; j += 32) cp_async_val(st + 2 * Nq + j, F + (size_t)e * Nt + j);
+    }
+    cp_async_commit();
+  };
+  const int e_first = blockIdx.x * nw + warp, e_step = gridDim.x * nw;
+  fetch(e_first, stage);
+  int buf = 0;
+  for (int e = e_first; e < a.n_e; e += e_step, buf ^= 1) {
+    const R* st = stage + buf * SV;
+    fetch(e + e_step, stage + (buf ^ 1) * SV);
+    // Jacobian coefficients of the bilinear map in the evaluation precision
+    // (FP64 arithmetic runs at a small fraction of the FP32 rate on this part)
+    R vx[4], vy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = a.cells[4 * (size_t)e + k];
+      vx[k] = (R)a.verts[2 * c];
+      vy[k] = (R)a.verts[2 * c + 1];
+    }
+    const R x1 = (R)0.25 * (-vx[0] + vx[1] + vx[2] - vx[3]), x2 = (R)0.25 * (-vx[0] - vx[1] + vx[2] + vx[3]);
+    const R x3 = (R)0.25 * (vx[0] - vx[1] + vx[2] - vx[3]);
+    const R y1 = (R)0.25 * (-vy[0] + vy[1] + vy[2] - vy[3]), y2 = (R)0.25 * (-vy[0] - vy[1] + vy[2] + vy[3]);
+    const R y3 = (R)0.25 * (vy[0] - vy[1] + vy[2] - vy[3]);
     const int64_t p0 = (int64_t)e * Nq;
+    cp_async_wait1();
+    __syncwarp();
     // point terms
     for (int q = lane; q < Nq; q += 32) {
       const int ia = q / Q, ib = q - ia * Q;
       const R s = xi[ia], t = xi[ib];
       const R x_xi = x1 + x3 * t, x_eta = x2 + x3 * s, y_xi = y1 + y3 * t, y_eta = y2 + y3 * s;
       const R w = wq[ia] * wq[ib];
-      const R ux = U[a.P_tot + p0 + q], uy = U[2 * a.P_tot + p0 + q];
+      const R ux = st[q], uy = st[Nq + q];
       P[q] = w * (y_eta * ux - x_eta * uy);
       Qm[q] = w * (x_xi * uy - y_xi * ux);
       if (NC == 3) C[q] = w * (x_xi * y_eta - x_eta * y_xi) * (bx * ux + by * uy);
@@ -89,6 +135,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
     for (int o = lane; o < TQ; o += 32) {
       const int m = o / Q, ib = o - m * Q;
       R s1 = 0, s2 = 0, s3 = 0;
+      #pragma unroll 4
       for (int ia = 0; ia < Q; ++ia) {
         s1 += dv[m * Q + ia] * P[ia * Q + ib];
         s2 += v[m * Q + ia] * Qm[ia * Q + ib];
@@ -103,11 +150,12 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
     for (int j = lane; j < Nt; j += 32) {
       const int m = j / T, n = j - m * T;
       R A = 0, B = 0;
+      #pragma unroll 4
       for (int ib = 0; ib < Q; ++ib) {
         A += T1[m * Q + ib] * v[n * Q + ib] + T2[m * Q + ib] * dv[n * Q + ib];
         if (NC == 3) B += T3[m * Q + ib] * v[n * Q + ib];
       }
-      const R Rv = eps * A + B - F[(size_t)e * Nt + j];
+      const R Rv = eps * A + B - st[2 * Nq + j];
       const R rb = rscale * Rv;
       Rb[j] = rb;
       lsum.add(Rv * Rv);
@@ -120,6 +168,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
       for (int o = lane; o < TQ; o += 32) {
         const int m = o / Q, ib = o - m * Q;
         R s1 = 0, s2 = 0;
+        #pragma unroll 4
         for (int n = 0; n < T; ++n) {
           s1 += Rb[m * T + n] * v[n * Q + ib];
           s2 += Rb[m * T + n] * dv[n * Q + ib];
@@ -132,6 +181,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
       for (int q = lane; q < Nq; q += 32) {
         const int ia = q / Q, ib = q - ia * Q;
         R sxi = 0, seta = 0, sv = 0;
+        #pragma unroll 4
         for (int m = 0; m < T; ++m) {
           sxi += dv[m * Q + ia] * T1[m * Q + ib];
           seta += v[m * Q + ia] * T2[m * Q + ib];
@@ -150,6 +200,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
     }
     __syncwarp();
   }
+  cp_async_wait0();
   // loss partials: per-thread compensated sums, a fixed-order tree in FP64 per warp, warps in order
   __shared__ double s_red[8][2];
   double l = (double)lsum.s - (double)lsum.c, d = (double)dsum.s - (double)dsum.c;
@@ -183,8 +234,20 @@ cudaError_t launch_mf(fv_ctx ctx, const MfArgs& a, int grid, int wpb, size_t sme
 
 }  // namespace
 
-// Warps per CTA (up to 8) such that tables and per-warp scratch fit in
-// about 96 KB; a grid-stride loop over elements, grid capped at 8 CTAs per SM.
+template <class R, int NC>
+int mf_blocks_per_sm(int wpb, size_t smem) {
+  int n = 0;
+  cudaFuncSetAttribute(contract_mfree<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_mfree<R, NC>, 32 * wpb, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return std::max(1, n);
+}
+
+// Warps per CTA (up to 8) such that tables and per-warp scratch fit in about
+// 96 KB; a persistent grid (resident CTAs per SM x SMs, at most one element
+// per warp) so that every warp streams several elements through its stages.
 void mfree_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* wpb, size_t* smem) {
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
   const size_t per_warp = (size_t)mf_warp_values(m->Q, m->T, m->n_comp) * rsz;
@@ -193,8 +256,15 @@ void mfree_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* wpb, s
   while (w > 1 && tables + w * per_warp > 96 * 1024) --w;
   *wpb = w;
   *smem = tables + w * per_warp;
+  int per_sm = 1;
+  if (*smem <= ctx->smem_optin) {
+    if (prec == FV_FP64)
+      per_sm = m->n_comp == 3 ? mf_blocks_per_sm<double, 3>(w, *smem) : mf_blocks_per_sm<double, 2>(w, *smem);
+    else
+      per_sm = m->n_comp == 3 ? mf_blocks_per_sm<float, 3>(w, *smem) : mf_blocks_per_sm<float, 2>(w, *smem);
+  }
   const int64_t blocks = (m->n_e + w - 1) / w;
-  *grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)ctx->n_sm * 8));
+  *grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)ctx->n_sm * per_sm));
 }
 
 int launch_contract_mfree(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, const void* U, void* UB,
