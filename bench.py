@@ -225,6 +225,81 @@ def run_reference(args, prob):
     return 0
 
 
+# ----------------------------------------------------------------------------- timing ablation
+ABL_NE = [1, 4, 16, 64, 256, 1024, 4096, 16384, 65536]
+ABL_Q = [4, 8, 12, 16, 20, 24, 28, 32]
+ABL_T = [2, 4, 6, 8, 10, 12, 14, 16]
+ABL_G_CAP = 4 << 30          # points whose stored G would exceed 4 GB are skipped
+
+
+def run_ablation(args):
+    """Median training-step time (loss + gradient + Adam update) over the
+    three hyperparameter panels of the paper's timing ablation (Sec. 5.8):
+    (a) N_test x N_quad at N_elem = 1, (b) N_elem x N_test at N_quad = 10 x 10,
+    (c) N_elem x N_quad at N_test = 10 x 10.  Poisson on the unit square with
+    u = sin(2 pi x) sin(2 pi y), uniform grids, 400 boundary points, a
+    2-30x3-1 network; FP32 and the FP16 tensor-core form."""
+    import torch
+    import fv_inputs as fi
+    from paper_2404_12063_b300 import api
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(local, stream)
+    u, f = fi.sinsin(2 * math.pi)
+    widths = [2, 30, 30, 30, 1]
+    params0 = fi.glorot_params(widths, 1, 1)
+    bd = fi.square_boundary_points(100)
+    steps = max(5, min(args.steps, 50))
+
+    def one(ne, Q, T):
+        gbytes = ne * 2 * (T * T) * (Q * Q) * 4
+        if gbytes > ABL_G_CAP:
+            return {"N_elem": ne, "N_quad": Q * Q, "N_test": T * T, "skipped": "G of %.1f GB" % (gbytes / 2 ** 30)}
+        n = int(round(math.sqrt(ne)))
+        prob = fi.Problem("ablation", fi.rect_grid(n, ne // n), Q, T, widths, params0, u, f, bd, u(bd[:, 0], bd[:, 1]))
+        row = {"N_elem": ne, "N_quad": Q * Q, "N_test": T * T, "G_MB": gbytes / 1e6}
+        for prec in ("fp32", "fp16"):
+            pb = api.problem_from_inputs(ctx, prob, prec, storage="fp32")
+            params = torch.tensor(params0, dtype=pb.dtype, device="cuda")
+            eps = torch.tensor([1.0], dtype=torch.float64, device="cuda")
+            adam = api.Adam(ctx, pb.net.n_params, prec)
+            grad = torch.empty_like(params)
+            out = torch.zeros(5, dtype=torch.float64, device="cuda")
+            fn = lambda: pb.inverse_step(params, eps, adam, 1e-3, grad, out)
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            row[prec + "_ms"] = statistics.median(ts)
+            del pb, adam
+        return row
+
+    panels = {"a_Ntest_x_Nquad_at_Nelem_1": [one(1, Q, T) for T in ABL_T for Q in ABL_Q],
+              "b_Nelem_x_Ntest_at_Nquad_100": [one(ne, 10, T) for ne in ABL_NE for T in ABL_T],
+              "c_Nelem_x_Nquad_at_Ntest_100": [one(ne, Q, 10) for ne in ABL_NE for Q in ABL_Q]}
+    done = [r["fp16_ms"] for pnl in panels.values() for r in pnl if "fp16_ms" in r]
+    line = {"metric": "median training-step time (loss + grad + Adam) over the N_quad x N_test x N_elem ablation grid",
+            "value": statistics.median(done) if done else None, "unit": "ms", "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 and f16/f32-accum", "data": "synthetic",
+            "config": {"workload": "poisson-unit-square ablation grid", "mlp": "2-30x3-1",
+                       "boundary_points": len(bd), "G_cap_GB": ABL_G_CAP / 2 ** 30,
+                       "grid": {"N_elem": ABL_NE, "Q": ABL_Q, "T": ABL_T}},
+            "panels": panels}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- batch workload
 def run_batch(args):
     """64 independent Poisson instances (uniform grids, N_e log-uniform in
@@ -309,13 +384,15 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="annulus", choices=["annulus", "batch"])
+    ap.add_argument("--workload", default="annulus", choices=["annulus", "batch", "ablation"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     import fv_inputs as fi
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     prob = fi.config3_annulus()
     if args.impl == "reference":
         return run_reference(args, prob)
