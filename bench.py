@@ -280,6 +280,20 @@ def run_ablation(args):
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
             row[prec + "_ms"] = statistics.median(ts)
+            # the same steps captured in a graph of 10 (fv_step_graph_create): no per-step host cost
+            g = api.StepGraph(pb, params, eps, adam, 1e-3, n_steps=10, grad=grad, out=out)
+            g.launch()
+            torch.cuda.synchronize()
+            tg = []
+            for _ in range(max(3, steps // 10)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.launch()
+                e1.record(stream)
+                e1.synchronize()
+                tg.append(e0.elapsed_time(e1) / 10)
+            row[prec + "_graph_ms"] = statistics.median(tg)
+            g.close()
             del pb, adam
         return row
 

@@ -265,6 +265,25 @@ typedef struct {
   double* out_dev;       /* device double[5] */
 } fv_instance;
 
+/* Captured training steps: n_steps consecutive fv_inverse_step calls with the
+ * same arguments (loss + gradient, then the Adam update when lr > 0; Sec. 4.5)
+ * recorded once into a CUDA graph, replayed by fv_graph_launch with one host
+ * call on the context's stream.  Small problems are bound by the host-side
+ * cost of issuing each step's launches; a graph removes it.  The graph owns a
+ * workspace sized at creation, and keeps the device pointers it was given
+ * (params, eps_dev, grad, out and the Adam state are updated in place on every
+ * replay; their contents may change between launches, the pointers may not).
+ * Results equal those of n_steps fv_inverse_step calls bitwise.  The handles
+ * (mesh, forcing, bc, adam) must outlive the graph.
+ * Errors: FV_ERR_ARG, FV_ERR_UNSUPPORTED (as fv_inverse_step), FV_ERR_OOM,
+ * FV_ERR_CUDA (capture or instantiation failed). */
+typedef struct fv_graph_s* fv_graph;
+int fv_step_graph_create(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                         void* params, double* eps_dev, const fv_eval_opts* opts, fv_adam adam, double lr,
+                         void* grad, double* out, int n_steps, fv_graph* out_graph);
+int fv_graph_launch(fv_graph graph);
+int fv_graph_destroy(fv_graph graph);
+
 /* Loss + gradient of n independent problems sharing one network shape and
  * options (each with its own mesh, forcing, boundary data, parameters and
  * outputs).  fv_batch_plan allocates a workspace per instance and captures

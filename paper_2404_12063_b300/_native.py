@@ -77,6 +77,10 @@ SIGNATURES = {
     "fv_adam_destroy": [_vp],
     "fv_inverse_step": [_vp, _vp, _vp, _vp, C.POINTER(fv_mlp_desc), _vp, _vp, C.POINTER(fv_eval_opts), _vp,
                         C.c_double, _vp, _vp],
+    "fv_step_graph_create": [_vp, _vp, _vp, _vp, C.POINTER(fv_mlp_desc), _vp, _vp, C.POINTER(fv_eval_opts), _vp,
+                             C.c_double, _vp, _vp, C.c_int, _pvp],
+    "fv_graph_launch": [_vp],
+    "fv_graph_destroy": [_vp],
     "fv_batch_plan": [_vp, C.c_int, C.POINTER(fv_instance), C.POINTER(fv_mlp_desc), C.POINTER(fv_eval_opts), C.c_int,
                       _pvp],
     "fv_batch_loss_grad": [_vp],

@@ -273,6 +273,43 @@ class Problem:
         return out, grad
 
 
+class StepGraph:
+    """n_steps training steps (loss + gradient + Adam) captured into one CUDA
+    graph (fv_step_graph_create); launch() replays them with one host call.
+    The tensors given at creation are updated in place on every launch."""
+
+    def __init__(self, problem: "Problem", params: torch.Tensor, eps_dev: torch.Tensor, adam: Optional["Adam"],
+                 lr: float, n_steps: int = 1, grad: Optional[torch.Tensor] = None,
+                 out: Optional[torch.Tensor] = None):
+        problem._check_params(params)
+        self.problem, self.params, self.eps_dev, self.adam = problem, params, eps_dev, adam
+        self.grad = torch.empty_like(params) if grad is None else grad
+        self.out = torch.zeros(5, dtype=torch.float64, device=params.device) if out is None else out
+        self.n_steps = n_steps
+        self._opts = problem.opts(eps_dev)
+        h = C.c_void_p()
+        N.call("fv_step_graph_create", problem.ctx.h, problem.mesh.h, problem.forcing.h,
+               problem.bc.h if problem.bc else None, C.byref(problem.net.desc), _ptr(params), _ptr(eps_dev),
+               C.byref(self._opts), adam.h if adam else None, float(lr), _ptr(self.grad), _ptr(self.out),
+               int(n_steps), C.byref(h))
+        self.h = h
+
+    def launch(self):
+        N.call("fv_graph_launch", self.h)
+        return self.out, self.grad
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.call("fv_graph_destroy", self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Adam:
     def __init__(self, ctx: Context, n_params: int, precision="fp32", beta1=0.9, beta2=0.999, eps=1e-8,
                  with_eps: bool = True):

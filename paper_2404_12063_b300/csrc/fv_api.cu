@@ -5,9 +5,44 @@
 #include <cstring>
 #include <mutex>
 
+#include <map>
+#include <tuple>
 #include "fv_internal.cuh"
 
 namespace fv {
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_set;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+}  // namespace
+
+cudaError_t ensure_smem_attr(fv_ctx ctx, const void* kernel, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  size_t& have = g_smem_set[{ctx->device, kernel}];
+  if (bytes <= have) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
+int occupancy(fv_ctx ctx, const void* kernel, int threads, size_t smem) {
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_occ.find({ctx->device, kernel, threads, smem});
+    if (it != g_occ.end()) return it->second;
+  }
+  if (ensure_smem_attr(ctx, kernel, smem) != cudaSuccess) { cudaGetLastError(); return 0; }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  g_occ[{ctx->device, kernel, threads, smem}] = n;
+  return n;
+}
+
 
 static thread_local char g_err[1024] = "";
 
@@ -172,18 +207,30 @@ __global__ void __launch_bounds__(256) seed_absmax_kernel(const float* __restric
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
 }
 
+// Adam (Kingma & Ba, bias-corrected) on theta and, when trained, eps.  The
+// bias corrections are computed once, in FP64, by one thread; the element
+// updates run in the parameters' precision (FP64 arithmetic is slow on this
+// part, and FP32 parameters gain nothing from it).
 template <class R>
 __global__ void adam_kernel(R* __restrict__ p, const R* __restrict__ g, int64_t n, R* __restrict__ m,
                             R* __restrict__ v, double* eps_p, const double* dLde, double* me, int with_eps, int* t,
                             double lr, double b1, double b2, double ae) {
+  __shared__ double s_c[2];
   const int tt = *t + 1;
-  const double c1 = 1.0 - pow(b1, (double)tt), c2 = 1.0 - pow(b2, (double)tt);
+  if (threadIdx.x == 0) {
+    s_c[0] = 1.0 - pow(b1, (double)tt);
+    s_c[1] = 1.0 - pow(b2, (double)tt);
+  }
+  __syncthreads();
+  const double c1 = s_c[0], c2 = s_c[1];
+  const R rb1 = (R)b1, rb2 = (R)b2, rc1 = (R)c1, rc2 = (R)c2, rlr = (R)lr, rae = (R)ae;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double gi = (double)g[i];
-    const double mi = b1 * (double)m[i] + (1.0 - b1) * gi;
-    const double vi = b2 * (double)v[i] + (1.0 - b2) * gi * gi;
-    m[i] = (R)mi; v[i] = (R)vi;
-    p[i] = (R)((double)p[i] - lr * (mi / c1) / (sqrt(vi / c2) + ae));
+    const R gi = g[i];
+    const R mi = rb1 * m[i] + ((R)1 - rb1) * gi;
+    const R vi = rb2 * v[i] + ((R)1 - rb2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] = p[i] - rlr * (mi / rc1) / (sqrt(vi / rc2) + rae);
   }
   if (with_eps && threadIdx.x == 0) {
     const double gi = dLde[0];
@@ -583,6 +630,25 @@ extern "C" int fv_adam_destroy(fv_adam a) {
   return FV_OK;
 }
 
+namespace fv {
+// One Adam update of (theta, eps) on the context's stream (Sec. 4.5: Adam).
+int launch_adam(fv_ctx ctx, fv_adam adam, void* params, const void* grad, double* eps_dev, double* out, double lr) {
+  cudaEvent_t ta;
+  time_begin(ctx, K_ADAM, &ta);
+  if (adam->prec == FV_FP64)
+    adam_kernel<double><<<1, 1024, 0, ctx->stream>>>((double*)params, (const double*)grad, adam->n, (double*)adam->m,
+                                                     (double*)adam->v, eps_dev, out + 4, adam->me, adam->with_eps,
+                                                     adam->t, lr, adam->beta1, adam->beta2, adam->eps);
+  else
+    adam_kernel<float><<<1, 1024, 0, ctx->stream>>>((float*)params, (const float*)grad, adam->n, (float*)adam->m,
+                                                    (float*)adam->v, eps_dev, out + 4, adam->me, adam->with_eps,
+                                                    adam->t, lr, adam->beta1, adam->beta2, adam->eps);
+  time_end(ctx, K_ADAM, ta);
+  FV_CUDA_TRY(cudaGetLastError());
+  return FV_OK;
+}
+}  // namespace fv
+
 extern "C" int fv_inverse_step(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
                                void* params, double* eps_dev, const fv_eval_opts* opts, fv_adam adam, double lr,
                                void* grad, double* out) {
@@ -596,18 +662,116 @@ extern "C" int fv_inverse_step(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_
   make_shape(mlp, &sh);
   FV_CHECK_ARG(adam->n == sh.n_params && adam->ctx == ctx, "fv_inverse_step: Adam state does not match");
   FV_CHECK_ARG((adam->prec == FV_FP64) == (opts->mlp_precision == FV_FP64), "fv_inverse_step: Adam precision");
-  cudaEvent_t ta;
-  time_begin(ctx, K_ADAM, &ta);
-  if (adam->prec == FV_FP64)
-    adam_kernel<double><<<1, 1024, 0, ctx->stream>>>((double*)params, (const double*)grad, adam->n, (double*)adam->m,
-                                                     (double*)adam->v, eps_dev, out + 4, adam->me, adam->with_eps,
-                                                     adam->t, lr, adam->beta1, adam->beta2, adam->eps);
-  else
-    adam_kernel<float><<<1, 1024, 0, ctx->stream>>>((float*)params, (const float*)grad, adam->n, (float*)adam->m,
-                                                    (float*)adam->v, eps_dev, out + 4, adam->me, adam->with_eps,
-                                                    adam->t, lr, adam->beta1, adam->beta2, adam->eps);
-  time_end(ctx, K_ADAM, ta);
-  FV_CUDA_TRY(cudaGetLastError());
+  return launch_adam(ctx, adam, params, grad, eps_dev, out, lr);
+}
+
+// ---------------------------------------------------------------- captured training steps
+// n_steps consecutive inverse steps (loss + gradient + Adam) captured once
+// into a CUDA graph; a launch replays them with one host call.  The graph
+// owns a workspace sized before capture, so nothing allocates inside it.
+struct fv_graph_s {
+  fv_ctx ctx = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* ws = nullptr;
+  int n_steps = 0;
+};
+
+static void graph_release(fv_graph g) {
+  if (!g) return;
+  if (g->ctx) cudaStreamSynchronize(g->ctx->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->capture) cudaStreamDestroy(g->capture);
+  if (g->ws) cudaFree(g->ws);
+  delete g;
+}
+
+extern "C" int fv_step_graph_create(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_mlp_desc* mlp,
+                                    void* params, double* eps_dev, const fv_eval_opts* opts, fv_adam adam, double lr,
+                                    void* grad, double* out, int n_steps, fv_graph* out_graph) {
+  clear_error();
+  FV_CHECK_ARG(ctx && mesh && forcing && mlp && params && eps_dev && opts && grad && out && out_graph,
+               "fv_step_graph_create: null argument");
+  FV_CHECK_ARG(n_steps >= 1 && n_steps <= 100000, "fv_step_graph_create: n_steps %d outside 1..100000", n_steps);
+  FV_CHECK_ARG(lr <= 0.0 || adam, "fv_step_graph_create: an Adam state is needed when lr > 0");
+  FV_CUDA_TRY(cudaSetDevice(ctx->device));
+  size_t need = 0;
+  int rc = evaluate(ctx, mesh, forcing, bc, mlp, params, opts, eps_dev, true, grad, out, nullptr, nullptr, nullptr,
+                    nullptr, 0, &need);
+  if (rc) return rc;
+  if (lr > 0.0) {
+    MlpShape sh;
+    make_shape(mlp, &sh);
+    FV_CHECK_ARG(adam->n == sh.n_params && adam->ctx == ctx, "fv_step_graph_create: Adam state does not match");
+    FV_CHECK_ARG((adam->prec == FV_FP64) == (opts->mlp_precision == FV_FP64), "fv_step_graph_create: Adam precision");
+  }
+  fv_graph g = new fv_graph_s();
+  g->ctx = ctx;
+  g->n_steps = n_steps;
+  auto fail = [&](int code) { graph_release(g); return code; };
+  cudaError_t e = cudaMalloc(&g->ws, std::max<size_t>(need, 256));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("fv_step_graph_create: %s", cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA);
+  }
+  fv_ctx_s cap_ctx;                           // same device, the capture stream, no timing
+  cap_ctx.device = ctx->device;
+  cap_ctx.stream = g->capture;
+  cap_ctx.n_sm = ctx->n_sm;
+  cap_ctx.smem_optin = ctx->smem_optin;
+  cap_ctx.smem_per_sm = ctx->smem_per_sm;
+  cap_ctx.err_dev = ctx->err_dev;
+  fv_mesh_s mesh_copy = *mesh;
+  mesh_copy.ctx = &cap_ctx;
+  fv_forcing_s forcing_copy = *forcing;
+  forcing_copy.mesh = &mesh_copy;
+  fv_bc_s bc_copy;
+  if (bc) { bc_copy = *bc; bc_copy.ctx = &cap_ctx; }
+  fv_adam_s adam_copy;
+  if (adam) { adam_copy = *adam; adam_copy.ctx = &cap_ctx; }
+  e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    set_error("fv_step_graph_create: capture failed to start (%s)", cudaGetErrorString(e));
+    return fail(FV_ERR_CUDA);
+  }
+  for (int k = 0; k < n_steps && rc == FV_OK; ++k) {
+    rc = evaluate(&cap_ctx, &mesh_copy, &forcing_copy, bc ? &bc_copy : nullptr, mlp, params, opts, eps_dev, true, grad,
+                  out, nullptr, nullptr, nullptr, g->ws, std::max<size_t>(need, 256));
+    if (rc == FV_OK && lr > 0.0) rc = launch_adam(&cap_ctx, &adam_copy, params, grad, eps_dev, out, lr);
+  }
+  cap_ctx.ws.ptr = nullptr;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(g->capture, &graph);
+  g->graph = graph;
+  if (rc) return fail(rc);
+  if (e != cudaSuccess) {
+    set_error("fv_step_graph_create: capture failed (%s)", cudaGetErrorString(e));
+    return fail(FV_ERR_CUDA);
+  }
+  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    set_error("fv_step_graph_create: instantiation failed (%s)", cudaGetErrorString(e));
+    return fail(FV_ERR_CUDA);
+  }
+  *out_graph = g;
+  return FV_OK;
+}
+
+extern "C" int fv_graph_launch(fv_graph g) {
+  clear_error();
+  FV_CHECK_ARG(g && g->exec, "fv_graph_launch: null graph");
+  FV_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  FV_CUDA_TRY(cudaGraphLaunch(g->exec, g->ctx->stream));
+  return FV_OK;
+}
+
+extern "C" int fv_graph_destroy(fv_graph g) {
+  clear_error();
+  graph_release(g);
   return FV_OK;
 }
 

@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) contract_direct(ContractArgs a) {
 template <class R, class Gt, int NC, int VEC, bool SKEW, int... Shape>
 cudaError_t launch_staged1(fv_ctx ctx, const ContractArgs& a, int grid, size_t smem) {
   auto kern = contract_staged<R, Gt, NC, VEC, SKEW, Shape...>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_attr(ctx, (const void*)kern, smem);
   if (e == cudaSuccess) kern<<<grid, kCThreads, smem, ctx->stream>>>(a);
   return e;
 }
@@ -576,7 +576,7 @@ int launch_t(fv_ctx ctx, const ContractArgs& a, bool staged, int vec, bool skew,
     e = a.n_comp == 3 ? launch_staged_vec<R, Gt, 3>(ctx, a, vec, skew, grid, smem)
                       : launch_staged_vec<R, Gt, 2>(ctx, a, vec, skew, grid, smem);
   } else {
-    e = cudaFuncSetAttribute(contract_direct<R, Gt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem_attr(ctx, (const void*)contract_direct<R, Gt>, smem);
     if (e == cudaSuccess) contract_direct<R, Gt><<<grid, kThreads, smem, ctx->stream>>>(a);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -605,7 +605,8 @@ int gcd_int(int a, int b) { return b ? gcd_int(b, a % b) : a; }
 // split factors minimise a per-element cost model counted in CTA-wide vector
 // steps (idle lanes included), preferring E small enough that four CTAs
 // share an SM.  Stages per CTA: double-buffered by default; one stage with up
-// to eight CTAs per SM where autotuning found that faster for the mesh.  The row pass rotates each lane's
+// to eight CTAs per SM where autotuning found that faster for the mesh, or
+// where an element block is too large for two stages.  The row pass rotates each lane's
 // chunk order when the row length in chunks shares a factor with the number
 // of lanes that one shared-memory wavefront serves.
 ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages = 0) {
@@ -651,6 +652,7 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
       P.grid = std::min<int>((m->n_e + E - 1) / E, ctx->n_sm * C);
     }
   }
+  if (!P.staged && S == 2 && !stages) return plan_contract(ctx, m, prec, 1);   // one stage per CTA
   if (!P.staged) {        // an element too large to stage: direct kernel
     P.smem = (size_t)m->Nt * 8 + kWarps * 4 * 8;
     P.grid = (int)std::min<int64_t>(m->n_e, (int64_t)ctx->n_sm * 8);

@@ -196,6 +196,13 @@ struct KahanR {
   }
 };
 
+// Launch attributes queried once per device and kernel (the queries cost
+// microseconds of host time each, which small problems would pay every call).
+// Raises the kernel's dynamic shared-memory limit to at least `bytes`.
+cudaError_t ensure_smem_attr(fv_ctx ctx, const void* kernel, size_t bytes);
+// Resident CTAs per SM for (kernel, threads, dynamic shared memory); 0 on error.
+int occupancy(fv_ctx ctx, const void* kernel, int threads, size_t smem);
+
 // ------------------------------------------------------------------ launchers
 // Each returns FV_OK or an error code and enqueues on ctx->stream.
 struct EvalPlan {

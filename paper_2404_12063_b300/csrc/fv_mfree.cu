@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
 
 template <class R, int NC>
 cudaError_t launch_mf(fv_ctx ctx, const MfArgs& a, int grid, int wpb, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(contract_mfree<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_attr(ctx, (const void*)contract_mfree<R, NC>, smem);
   if (e == cudaSuccess) contract_mfree<R, NC><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
   return e;
 }
@@ -235,14 +235,8 @@ cudaError_t launch_mf(fv_ctx ctx, const MfArgs& a, int grid, int wpb, size_t sme
 }  // namespace
 
 template <class R, int NC>
-int mf_blocks_per_sm(int wpb, size_t smem) {
-  int n = 0;
-  cudaFuncSetAttribute(contract_mfree<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contract_mfree<R, NC>, 32 * wpb, smem) != cudaSuccess) {
-    cudaGetLastError();
-    n = 1;
-  }
-  return std::max(1, n);
+int mf_blocks_per_sm(fv_ctx ctx, int wpb, size_t smem) {
+  return std::max(1, occupancy(ctx, (const void*)contract_mfree<R, NC>, 32 * wpb, smem));
 }
 
 // Warps per CTA (up to 8) such that tables and per-warp scratch fit in about
@@ -259,9 +253,9 @@ void mfree_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* wpb, s
   int per_sm = 1;
   if (*smem <= ctx->smem_optin) {
     if (prec == FV_FP64)
-      per_sm = m->n_comp == 3 ? mf_blocks_per_sm<double, 3>(w, *smem) : mf_blocks_per_sm<double, 2>(w, *smem);
+      per_sm = m->n_comp == 3 ? mf_blocks_per_sm<double, 3>(ctx, w, *smem) : mf_blocks_per_sm<double, 2>(ctx, w, *smem);
     else
-      per_sm = m->n_comp == 3 ? mf_blocks_per_sm<float, 3>(w, *smem) : mf_blocks_per_sm<float, 2>(w, *smem);
+      per_sm = m->n_comp == 3 ? mf_blocks_per_sm<float, 3>(ctx, w, *smem) : mf_blocks_per_sm<float, 2>(ctx, w, *smem);
   }
   const int64_t blocks = (m->n_e + w - 1) / w;
   *grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)ctx->n_sm * per_sm));

@@ -512,7 +512,7 @@ int launch_fwd_t(fv_ctx ctx, const EvalPlan& pl, const void* params, const doubl
   const int64_t n_tiles = (pl.P_tot + a.TP - 1) / a.TP;
   const int per_sm = std::max<int>(1, (int)(std::min<size_t>(ctx->smem_optin, 228 * 1024) / (smem + 1024)));
   const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)ctx->n_sm * std::min(per_sm, 4));
-  cudaError_t e = cudaFuncSetAttribute(mlp_fwd_simt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_attr(ctx, (const void*)mlp_fwd_simt<R>, smem);
   if (e == cudaSuccess) {
     mlp_fwd_simt<R><<<grid, kThreads, smem, ctx->stream>>>(a);
     e = cudaGetLastError();
@@ -546,7 +546,7 @@ int launch_bwd_t(fv_ctx ctx, const EvalPlan& pl, const void* params, const doubl
   if (rc) return rc;
   a.params = params; a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot; a.UB = UB; a.gpart = gpart;
   *nb = grid;
-  cudaError_t e = cudaFuncSetAttribute(mlp_bwd_simt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_attr(ctx, (const void*)mlp_bwd_simt<R>, smem);
   if (e == cudaSuccess) {
     mlp_bwd_simt<R><<<grid, kThreads, smem, ctx->stream>>>(a);
     e = cudaGetLastError();

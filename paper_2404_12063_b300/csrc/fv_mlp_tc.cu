@@ -839,24 +839,16 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
 // Resident CTAs per SM: the hardware occupancy (registers, shared memory)
 // capped so that their tensor-memory allocations fit in 512 columns.
 template <int HP, class OP>
-int tc_ctas_per_sm(const TcPlan& p, bool reverse) {
-  int n = 0;
-  cudaError_t e;
-  if (reverse) {
-    cudaFuncSetAttribute(mlp_bwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_bwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
-  } else {
-    cudaFuncSetAttribute(mlp_fwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mlp_fwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
-  }
-  if (e != cudaSuccess || n < 1) n = 1;
-  return std::max(1, std::min(n, 512 / p.tmem_cols));
+int tc_ctas_per_sm(fv_ctx ctx, const TcPlan& p, bool reverse) {
+  const int n = reverse ? occupancy(ctx, (const void*)mlp_bwd_tc<HP, OP>, tc_threads<HP>(), p.smem)
+                        : occupancy(ctx, (const void*)mlp_fwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
+  return std::max(1, std::min(std::max(n, 1), 512 / p.tmem_cols));
 }
 
 int tc_grid(fv_ctx ctx, const TcPlan& p, bool reverse, bool fp16, int64_t P_tot) {
   const int64_t n_tiles = (P_tot + kTile - 1) / kTile;
-  const int per = p.HP == 32 ? (fp16 ? tc_ctas_per_sm<32, OpF16>(p, reverse) : tc_ctas_per_sm<32, OpBF16>(p, reverse))
-                             : (fp16 ? tc_ctas_per_sm<64, OpF16>(p, reverse) : tc_ctas_per_sm<64, OpBF16>(p, reverse));
+  const int per = p.HP == 32 ? (fp16 ? tc_ctas_per_sm<32, OpF16>(ctx, p, reverse) : tc_ctas_per_sm<32, OpBF16>(ctx, p, reverse))
+                             : (fp16 ? tc_ctas_per_sm<64, OpF16>(ctx, p, reverse) : tc_ctas_per_sm<64, OpBF16>(ctx, p, reverse));
   return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)ctx->n_sm * per));
 }
 
@@ -864,10 +856,10 @@ template <int HP, class OP>
 int launch_tc(fv_ctx ctx, const TcArgs& a, bool reverse, int grid) {
   cudaError_t e;
   if (reverse) {
-    e = cudaFuncSetAttribute(mlp_bwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    e = ensure_smem_attr(ctx, (const void*)mlp_bwd_tc<HP, OP>, a.pl.smem);
     if (e == cudaSuccess) mlp_bwd_tc<HP, OP><<<grid, tc_threads<HP>(), a.pl.smem, ctx->stream>>>(a);
   } else {
-    e = cudaFuncSetAttribute(mlp_fwd_tc<HP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.pl.smem);
+    e = ensure_smem_attr(ctx, (const void*)mlp_fwd_tc<HP, OP>, a.pl.smem);
     if (e == cudaSuccess) mlp_fwd_tc<HP, OP><<<grid, tc_threads<HP>(), a.pl.smem, ctx->stream>>>(a);
   }
   if (e == cudaSuccess) e = cudaGetLastError();

@@ -35,3 +35,33 @@ def test_inverse_problem_eps_moves_to_truth(ctx):
     h = train.train(ctx, prob, "fp32", epochs=1500, lr=1e-2, every=500, train_eps=True)
     eps_path = [r[4] for r in h]
     assert abs(eps_path[-1] - 0.3) < 0.5 * abs(eps_path[0] - 0.3)
+
+
+@pytest.mark.parametrize("k,precision", [(4, "fp32"), (2, "fp16"), (1, "fp64")])
+def test_step_graph_equals_individual_steps(ctx, k, precision):
+    """A captured graph of n training steps (loss + grad + Adam) gives bitwise
+    the parameters, eps, gradient and loss of n fv_inverse_step calls."""
+    from paper_2404_12063_b300 import api
+    prob = fi.CONFIGS[k]()
+    pb = api.problem_from_inputs(ctx, prob, precision)
+    n = 4
+    res = []
+    for graph in (False, True):
+        params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+        eps = torch.tensor([prob.eps], dtype=torch.float64, device="cuda")
+        adam = api.Adam(ctx, pb.net.n_params, precision, with_eps=(k == 4))
+        grad = torch.empty_like(params)
+        out = torch.zeros(5, dtype=torch.float64, device="cuda")
+        if graph:
+            g = api.StepGraph(pb, params, eps, adam, 1e-3, n_steps=n, grad=grad, out=out)
+            g.launch()
+            g.launch()
+        else:
+            for _ in range(2 * n):
+                pb.inverse_step(params, eps, adam, 1e-3, grad, out)
+        torch.cuda.synchronize()
+        res.append((params.clone(), eps.clone(), grad.clone(), out.clone()))
+        if graph:
+            g.close()
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
