@@ -423,4 +423,26 @@ def config5_batch(n_instances: int = 64, seed: int = 4) -> List[Problem]:
     return out
 
 
+def config_eps_field() -> Problem:
+    """Space-dependent diffusion (Sec. 4.7.2): -div(eps(x, y) grad u) + b . grad u = f
+    on the 1024-element disc of config 2 (Q=8, T=6), f = 10, b = (1, 0); one
+    network 2-30x3-2 with outputs (u, eps) (seed 5); 1000 boundary points with
+    g = 0 and 500 sensors (seed 5, stream 2) in the disc.  The paper's sensor
+    data come from a finite-element reference that is not available; the
+    synthetic observations are u_obs = 5 (1 - x^2 - y^2), the solution of
+    -0.5 Lap u = 10 with u = 0 on the circle."""
+    base = disc_butterfly(16, 12)
+    mesh = jitter_nodes(base, ~boundary_nodes_of(base), 0.2, seed=1)
+    widths = [2, 30, 30, 30, 2]
+    u_obs = lambda x, y: 5.0 * (1.0 - x * x - y * y)
+    f = lambda x, y: 10.0 + 0.0 * x
+    bd = circle_points(1000)
+    r = np.sqrt(SplitMix64(5, 2).uniforms(500))
+    th = 2 * math.pi * SplitMix64(5, 3).uniforms(500)
+    sens = np.stack([0.95 * r * np.cos(th), 0.95 * r * np.sin(th)], axis=1)
+    return Problem("eps-field-disc-1024", mesh, 8, 6, widths, glorot_params(widths, 5, 1), u_obs, f,
+                   bd, np.zeros(len(bd)), eps=1.0, b=(1.0, 0.0), tau=10.0,
+                   sensor_xy=sens, sensor_u=u_obs(sens[:, 0], sens[:, 1]), gamma=10.0, precision="fp32")
+
+
 CONFIGS = {1: config1_tiny, 2: config2_disc, 3: config3_annulus, 4: config4_inverse}

@@ -120,6 +120,15 @@ def mlp(widths, params, xy):
     return u, ux, uy
 
 
+def mlp_eps(widths, params, xy):
+    """Second output eps(x, y) of a two-output network."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    p, xy = _d(params), _d(xy).reshape(-1, 2)
+    e = np.zeros(xy.shape[0])
+    lib().oracle_mlp_eps(len(widths) - 1, _ptr(w, _ip), _ptr(p), xy.shape[0], _ptr(xy), _ptr(e))
+    return e
+
+
 def mlp_cstep_x(widths, params, xy, h=1e-30):
     w = np.ascontiguousarray(widths, dtype=np.int32)
     p, xy = _d(params), _d(xy).reshape(-1, 2)
@@ -159,7 +168,7 @@ class Bound:
         self.n_params = int(sum(prob.widths[i + 1] * (prob.widths[i] + 1) for i in range(len(prob.widths) - 1)))
 
     def loss_grad(self, params, eps: Optional[float] = None, want_grad=True, want_R=False, want_ubar=False,
-                  want_upts=False, n_threads: int = 1):
+                  want_upts=False, n_threads: int = 1, want_eps_field=False):
         p = _d(params)
         eps = self.prob.eps if eps is None else eps
         n_e, Nt, Nq = self.cells.shape[0], self.prob.test_order ** 2, self.prob.quad_order ** 2
@@ -169,8 +178,10 @@ class Bound:
         R = np.zeros((n_e, Nt)) if want_R else None
         ub = np.zeros((n_e, Nq, 2)) if want_ubar else None
         up = np.zeros((n_e, Nq, 3)) if want_upts else None
+        eb = np.zeros((n_e, Nq)) if want_eps_field else None
+        ep = np.zeros((n_e, Nq)) if want_eps_field else None
         rc = lib().oracle_loss_grad(C.byref(self.s), _ptr(p), C.c_double(eps), _ptr(loss4), _ptr(g), _ptr(de),
-                                    _ptr(R), _ptr(ub), _ptr(up), n_threads)
+                                    _ptr(R), _ptr(ub), _ptr(up), n_threads, _ptr(eb), _ptr(ep))
         if rc != 0:
             raise ValueError("oracle_loss_grad failed (%d)" % rc)
         out = {"loss": loss4[0], "Lv": loss4[1], "Lb": loss4[2], "Ls": loss4[3], "dL_deps": de[0]}
@@ -182,6 +193,9 @@ class Bound:
             out["ubar"] = ub
         if want_upts:
             out["upts"] = up
+        if want_eps_field:
+            out["ebar"] = eb          # dL/deps(x_q) of a two-output network
+            out["epts"] = ep          # eps(x_q)
         return out
 
     def loss_value(self, params, eps: Optional[float] = None, want_R=False):

@@ -17,6 +17,8 @@
 //     PINNs_Loss_components) and gamma L_s (Sec. 4.7)
 //   * bilinear map, its Jacobian and inverse (App. A.1)
 //   * Gauss-Lobatto-Legendre quadrature and test functions v_n = P_{n+1} - P_{n-1} (Sec. 4.5)
+//   * space-dependent diffusion (Sec. 4.7.2): a network with two outputs (u, eps);
+//     eps(x, y) replaces the scalar eps in the diffusion term at every node
 //
 // Readings taken where the paper is silent or garbled:
 //   - the printed inverse Jacobian (App. A.1) swaps xi and eta in its second
@@ -24,6 +26,9 @@
 //   - the convection term b.grad u tested against v, with eps multiplying only
 //     the diffusion term (Alg. 3 prints only the diffusion terms).
 //   - test index j = (m-1) T + (n-1), m along xi; quadrature index q = a Q + b, a along xi.
+//   - with two outputs, the second output is eps(x, y) itself (linear output, no
+//     activation): the paper states that the network outputs both fields and
+//     names no transform.  Boundary and sensor terms use the first output only.
 //
 // Gradients: a hand-written reverse sweep (FP64).  The same loss is also
 // instantiated on std::complex<double> so that complex-step derivatives
@@ -150,9 +155,10 @@ struct Net {
 // Forward pass with forward-mode tangents d/dx, d/dy (chain rule through each
 // layer: z = W h + b, z' = W h', t = tanh z, t' = (1 - t^2) z').
 // If `tape` is given, records per hidden layer t, z'_x, z'_y for the reverse sweep.
+// With two outputs, *e_out receives the second output's value (eps(x, y)).
 template <class T>
 void mlp_forward(const Net& net, const T* p, T x, T y, T* u, T* ux, T* uy,
-                 std::vector<T>* tape = nullptr) {
+                 std::vector<T>* tape = nullptr, T* e_out = nullptr) {
   const int mw = net.max_width();
   std::vector<T> h(mw), hx(mw), hy(mw), nh(mw), nhx(mw), nhy(mw);
   h[0] = x; h[1] = y;
@@ -182,12 +188,14 @@ void mlp_forward(const Net& net, const T* p, T x, T y, T* u, T* ux, T* uy,
     std::swap(h, nh); std::swap(hx, nhx); std::swap(hy, nhy);
   }
   *u = h[0]; *ux = hx[0]; *uy = hy[0];
+  if (e_out) *e_out = net.w[net.L] > 1 ? h[1] : T(0.0);
 }
 
-// Reverse sweep through mlp_forward for seeds (ub, uxb, uyb) on (u, u_x, u_y);
-// adds d/dtheta into g.  Uses the tape written by mlp_forward at the same point.
+// Reverse sweep through mlp_forward for seeds (ub, uxb, uyb) on (u, u_x, u_y)
+// and, with two outputs, eb on the second output's value; adds d/dtheta into g.
+// Uses the tape written by mlp_forward at the same point.
 void mlp_reverse(const Net& net, const double* p, double x, double y, const std::vector<double>& tape,
-                 double ub, double uxb, double uyb, double* g) {
+                 double ub, double uxb, double uyb, double* g, double eb = 0.0) {
   const int L = net.L;
   // rebuild layer inputs from the tape: input of layer i is the output of layer i-1
   std::vector<size_t> toff(L, 0);
@@ -206,6 +214,7 @@ void mlp_reverse(const Net& net, const double* p, double x, double y, const std:
   std::vector<double> zb(mw), zxb(mw), zyb(mw), hb(mw), hxb(mw), hyb(mw);
   // output layer (linear): seeds are the adjoints of z, z'_x, z'_y directly
   zb[0] = ub; zxb[0] = uxb; zyb[0] = uyb;
+  if (net.w[L] > 1) { zb[1] = eb; zxb[1] = 0.0; zyb[1] = 0.0; }
   for (int i = L - 1; i >= 0; --i) {
     const int nin = net.w[i], nout = net.w[i + 1];
     const double* W = p + net.off[i];
@@ -316,6 +325,15 @@ void oracle_mlp(int n_layers, const int* widths, const double* p, int n, const d
                 double* u, double* ux, double* uy) {
   Net net(n_layers, widths);
   for (int i = 0; i < n; ++i) mlp_forward<double>(net, p, xy[2 * i], xy[2 * i + 1], &u[i], &ux[i], &uy[i]);
+}
+
+// Second output (eps(x, y)) of a two-output network at n points.
+void oracle_mlp_eps(int n_layers, const int* widths, const double* p, int n, const double* xy, double* eps) {
+  Net net(n_layers, widths);
+  for (int i = 0; i < n; ++i) {
+    double u, ux, uy;
+    mlp_forward<double>(net, p, xy[2 * i], xy[2 * i + 1], &u, &ux, &uy, nullptr, &eps[i]);
+  }
 }
 
 // Complex-step d u/dx and d u/dy of the MLP value (independent of the tangent code path).
@@ -460,8 +478,9 @@ void loss_generic(const OracleProblem* pb, const Net& net, const S* p, S eps, S*
       for (int b = 0; b < Q; ++b) {
         const int q = a * Q + b;
         Geo g = bilinear(vx, vy, xs[a], xs[b]);
-        S u, ux, uy;
-        mlp_forward<S>(net, p, S(g.x), S(g.y), &u, &ux, &uy);
+        S u, ux, uy, ep;
+        mlp_forward<S>(net, p, S(g.x), S(g.y), &u, &ux, &uy, nullptr, &ep);
+        const S epq = net.w[net.L] > 1 ? ep : eps;     // eps(x, y) or the scalar
         const double wq = ws[a] * ws[b];
         const double fq = pb->f_quad[(size_t)e * Nq + q];
         for (int m = 1; m <= T; ++m)
@@ -473,7 +492,7 @@ void loss_generic(const OracleProblem* pb, const Net& net, const S* p, S eps, S*
             const double v_x = (g.y_eta * v_xi - g.y_xi * v_eta) / g.D;
             const double v_y = (-g.x_eta * v_xi + g.x_xi * v_eta) / g.D;
             R[(m - 1) * T + (n - 1)] +=
-                wq * g.D * (eps * (ux * v_x + uy * v_y) + (pb->bx * ux + pb->by * uy) * v - fq * v);
+                wq * g.D * (epq * (ux * v_x + uy * v_y) + (pb->bx * ux + pb->by * uy) * v - fq * v);
           }
       }
     for (int j = 0; j < Nt; ++j) {
@@ -510,8 +529,12 @@ extern "C" {
 //   upts: [n_e][Q*Q][3] (u, u_x, u_y) at the quadrature nodes, or null.
 // Elements are split over n_threads OpenMP threads (each with its own gradient
 // buffer; the buffers are summed in thread order).
+//   ebar: [n_e][Q*Q] adjoint seed dL/deps(x_q) of a two-output network, or null;
+//   epts: [n_e][Q*Q] eps(x_q) of a two-output network, or null.
+// With two outputs dL_deps is 0 (eps is part of theta).
 int oracle_loss_grad(const OracleProblem* pb, const double* p, double eps, double* loss4, double* grad,
-                     double* dL_deps, double* R_out, double* ubar_out, double* upts_out, int n_threads) {
+                     double* dL_deps, double* R_out, double* ubar_out, double* upts_out, int n_threads,
+                     double* ebar_out, double* epts_out) {
   const int Q = pb->Q, T = pb->T, Nq = Q * Q, Nt = T * T;
   std::vector<double> xs, ws;
   if (!gll(Q, xs, ws) || T < 1 || pb->n_layers < 1) return 1;
@@ -531,15 +554,18 @@ int oracle_loss_grad(const OracleProblem* pb, const double* p, double eps, doubl
     double vx[4], vy[4];
     cell_vertices(pb->vertices, pb->cells, e, vx, vy);
     std::vector<double> R(Nt, 0.0), A(Nt, 0.0);
-    std::vector<double> U(Nq), UX(Nq), UY(Nq);
+    std::vector<double> U(Nq), UX(Nq), UY(Nq), EP(Nq, eps);
     std::vector<Geo> geo(Nq);
     std::vector<std::vector<double>> tapes(Nq);
+    const bool two = net.w[net.L] > 1;
     // value + gradient of the network at every node, then the residual sums
     for (int a = 0; a < Q; ++a)
       for (int b = 0; b < Q; ++b) {
         const int q = a * Q + b;
         geo[q] = bilinear(vx, vy, xs[a], xs[b]);
-        mlp_forward<double>(net, p, geo[q].x, geo[q].y, &U[q], &UX[q], &UY[q], grad ? &tapes[q] : nullptr);
+        double ep = 0.0;
+        mlp_forward<double>(net, p, geo[q].x, geo[q].y, &U[q], &UX[q], &UY[q], grad ? &tapes[q] : nullptr, &ep);
+        if (two) EP[q] = ep;
       }
     for (int a = 0; a < Q; ++a)
       for (int b = 0; b < Q; ++b) {
@@ -558,7 +584,7 @@ int oracle_loss_grad(const OracleProblem* pb, const double* p, double eps, doubl
             const int j = (m - 1) * T + (n - 1);
             const double diff = wq * g.D * (UX[q] * v_x + UY[q] * v_y);
             A[j] += diff;
-            R[j] += eps * diff + wq * g.D * ((pb->bx * UX[q] + pb->by * UY[q]) * v - fq * v);
+            R[j] += EP[q] * diff + wq * g.D * ((pb->bx * UX[q] + pb->by * UY[q]) * v - fq * v);
           }
       }
     double lv = 0.0, de = 0.0;
@@ -568,20 +594,22 @@ int oracle_loss_grad(const OracleProblem* pb, const double* p, double eps, doubl
       if (R_out) R_out[(size_t)e * Nt + j] = R[j];
     }
     lv_e[e] = lv;
-    de_e[e] = de;
+    de_e[e] = two ? 0.0 : de;
+    if (epts_out)
+      for (int q = 0; q < Nq; ++q) epts_out[(size_t)e * Nq + q] = two ? EP[q] : 0.0;
     if (upts_out)
       for (int q = 0; q < Nq; ++q) {
         double* o = upts_out + ((size_t)e * Nq + q) * 3;
         o[0] = U[q]; o[1] = UX[q]; o[2] = UY[q];
       }
-    if (grad || ubar_out) {
+    if (grad || ubar_out || ebar_out) {
       // adjoint seeds at each node: dL/du_x = sum_j Rbar_j w D (eps dv_j/dx + bx v_j), likewise y
       for (int a = 0; a < Q; ++a)
         for (int b = 0; b < Q; ++b) {
           const int q = a * Q + b;
           const Geo& g = geo[q];
           const double wq = ws[a] * ws[b];
-          double sx = 0.0, sy = 0.0;
+          double sx = 0.0, sy = 0.0, eb = 0.0;
           for (int m = 1; m <= T; ++m)
             for (int n = 1; n <= T; ++n) {
               double vm, dvm, vn, dvn;
@@ -591,14 +619,16 @@ int oracle_loss_grad(const OracleProblem* pb, const double* p, double eps, doubl
               const double v_x = (g.y_eta * v_xi - g.y_xi * v_eta) / g.D;
               const double v_y = (-g.x_eta * v_xi + g.x_xi * v_eta) / g.D;
               const double Rb = rscale * R[(m - 1) * T + (n - 1)];
-              sx += Rb * wq * g.D * (eps * v_x + pb->bx * v);
-              sy += Rb * wq * g.D * (eps * v_y + pb->by * v);
+              sx += Rb * wq * g.D * (EP[q] * v_x + pb->bx * v);
+              sy += Rb * wq * g.D * (EP[q] * v_y + pb->by * v);
+              eb += Rb * wq * g.D * (UX[q] * v_x + UY[q] * v_y);   // d R_j / d eps(x_q)
             }
           if (ubar_out) {
             ubar_out[((size_t)e * Nq + q) * 2] = sx;
             ubar_out[((size_t)e * Nq + q) * 2 + 1] = sy;
           }
-          if (grad) mlp_reverse(net, p, g.x, g.y, tapes[q], 0.0, sx, sy, gbuf[tid].data());
+          if (ebar_out) ebar_out[(size_t)e * Nq + q] = two ? eb : 0.0;
+          if (grad) mlp_reverse(net, p, g.x, g.y, tapes[q], 0.0, sx, sy, gbuf[tid].data(), two ? eb : 0.0);
         }
     }
   }

@@ -433,3 +433,64 @@ def test_inverse_problem_source_term():
     h = 1e-4
     np.testing.assert_allclose(up(x, 0), (u(x + h, 0) - u(x - h, 0)) / (2 * h), atol=1e-7)
     np.testing.assert_allclose(upp(x, 0), (u(x + h, 0) - 2 * u(x, 0) + u(x - h, 0)) / h ** 2, atol=1e-5)
+
+
+# ---------------------------------------------------------------- space-dependent eps (Sec. 4.7.2)
+def _two_output_params(widths1, params1, eps0):
+    """A two-output network whose second output is the constant eps0: the
+    first output's weights are params1's, the eps row is zero, its bias eps0."""
+    n_in = widths1[-2]
+    head = params1[:len(params1) - (n_in + 1)]
+    W_u, b_u = params1[len(params1) - (n_in + 1): len(params1) - 1], params1[-1]
+    return np.concatenate([head, W_u, np.zeros(n_in), [b_u, eps0]])
+
+
+def test_eps_field_reduces_to_constant_eps():
+    """A two-output network with a constant second output eps0 gives the loss of
+    the scalar-eps problem at eps0, the same gradient on the shared weights, and
+    on the eps bias exactly dL/deps of the scalar problem (which is pinned by
+    complex step above)."""
+    mesh = _skewed_mesh(2, seed=5)
+    widths1 = [2, 6, 5, 1]
+    params1 = fi.random_bias_params(widths1, 4, 1, gain=1.2)
+    u, f = fi.sinsin(2 * math.pi)
+    bd = fi.square_boundary_points(5)
+    eps0 = 0.65
+    prob1 = fi.Problem("tiny", mesh, 5, 4, widths1, params1, u, f, bd, u(bd[:, 0], bd[:, 1]), eps=eps0,
+                       b=(0.3, -0.2), tau=2.0)
+    widths2 = widths1[:-1] + [2]
+    params2 = _two_output_params(widths1, params1, eps0)
+    prob2 = fi.Problem("tiny2", mesh, 5, 4, widths2, params2, u, f, bd, u(bd[:, 0], bd[:, 1]), eps=123.0,
+                       b=(0.3, -0.2), tau=2.0)
+    r1 = oracle.Bound(prob1).loss_grad(params1)
+    r2 = oracle.Bound(prob2).loss_grad(params2, want_eps_field=True)
+    assert abs(r2["loss"] - r1["loss"]) < 1e-13 * abs(r1["loss"])
+    n_in = widths1[-2]
+    head = len(params1) - (n_in + 1)
+    np.testing.assert_allclose(r2["grad"][:head + n_in], r1["grad"][:head + n_in], rtol=1e-12, atol=1e-15)
+    assert abs(r2["grad"][head + 2 * n_in] - r1["grad"][-1]) < 1e-12 * abs(r1["grad"][-1])     # b_u
+    assert abs(r2["grad"][-1] - r1["dL_deps"]) < 1e-12 * abs(r1["dL_deps"])                    # b_eps
+    assert r2["dL_deps"] == 0.0
+    np.testing.assert_allclose(r2["epts"], eps0, rtol=0, atol=1e-15)
+    # the eps seeds sum to dL/deps over the whole mesh
+    assert abs(r2["ebar"].sum() - r1["dL_deps"]) < 1e-12 * abs(r1["dL_deps"])
+
+
+def test_eps_field_gradient_complex_step():
+    """Every parameter of a two-output network (u, eps(x, y)) on a tiny CD2D
+    problem with boundary and sensor terms, against complex-step derivatives
+    of the loss (the generic loss code shares nothing with the reverse sweep)."""
+    mesh = _skewed_mesh(2, seed=6)
+    widths = [2, 5, 6, 2]
+    params = fi.random_bias_params(widths, 11, 1, gain=1.1)
+    u, f = fi.sinsin(2 * math.pi)
+    bd = fi.square_boundary_points(4)
+    sens = fi.uniform_points(5, 12, 2, 0, 1)
+    prob = fi.Problem("tiny-eps-field", mesh, 5, 4, widths, params, u, f, bd, u(bd[:, 0], bd[:, 1]), eps=7.0,
+                      b=(0.5, 0.25), tau=1.5, sensor_xy=sens, sensor_u=u(sens[:, 0], sens[:, 1]) + 0.05, gamma=3.0)
+    b = oracle.Bound(prob)
+    out = b.loss_grad(params)
+    cs = b.cstep(params, np.arange(len(params)))
+    np.testing.assert_allclose(out["grad"], cs, rtol=1e-11, atol=1e-13 * np.abs(cs).max())
+    # eps(x, y) really is the second output: the loss moves with its bias
+    assert abs(cs[-1]) > 1e-6
