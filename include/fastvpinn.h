@@ -67,11 +67,16 @@ typedef struct fv_forcing_s* fv_forcing;
 typedef struct fv_bc_s* fv_bc;
 typedef struct fv_adam_s* fv_adam;
 
-/* Network shape: widths[0] = 2 (x, y), widths[n_layers] = 1 (u), hidden
+/* Network shape: widths[0] = 2 (x, y), widths[n_layers] = 1 (u) or 2 (u and
+ * the diffusion coefficient eps(x, y), the space-dependent inverse problem of
+ * Sec. 4.7.2: the second output is eps itself, linear, and replaces the scalar
+ * eps of fv_eval_opts in the diffusion term at every quadrature point; such
+ * networks run in FP64 / FP32 and use the matrix-free contraction), hidden
  * widths in [1, 128]; 2..12 affine maps (at least one hidden layer); tanh
  * after every map but the last (Sec. 2.2, Eq. NN).  The parameters (and, for
  * the reverse sweep, an FP64 copy of their gradient) must fit in one CTA's
- * shared memory; larger networks return FV_ERR_UNSUPPORTED. */
+ * shared memory; larger networks return FV_ERR_UNSUPPORTED.  The last map's
+ * parameters are W_L (row-major [outputs][inputs]) then b_L, as for every map. */
 typedef struct {
   int n_layers;
   const int* widths; /* host, n_layers + 1 entries */
@@ -224,8 +229,9 @@ int fv_loss_grad_noalloc(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc,
 
 /* Inspection: one loss + gradient evaluation that also copies out its
  * intermediates (synchronises the stream):
- *   U_dev  [3][P_tot]   u, du/dx, du/dy at the quadrature points then the boundary and sensor points
- *   UB_dev [3][P_tot]   adjoint seeds dL/du, dL/du_x, dL/du_y at the same points
+ *   U_dev  [S][P_tot]   u, du/dx, du/dy (, eps(x, y)) at the quadrature points then the boundary and
+ *                       sensor points; S = 3, or 4 for a two-output network
+ *   UB_dev [S][P_tot]   adjoint seeds dL/du, dL/du_x, dL/du_y (, dL/deps(x, y)) at the same points
  *   R_dev  [n_elements][T*T] (double) element residuals R[e][j]
  * U_dev / UB_dev are in the network precision (FP64 or FP32); any of the three
  * may be NULL.  out_dev as for fv_loss_grad.  Allocates a temporary gradient. */
@@ -233,8 +239,9 @@ int fv_eval_intermediates(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc
                           const void* params_dev, const fv_eval_opts* opts, void* U_dev, void* UB_dev,
                           double* R_dev, double* out_dev);
 
-/* Point values: u, du/dx, du/dy of the network at n points (device [n][2]
- * FP64 in, device [3][n] out in the params' precision). */
+/* Point values: u, du/dx, du/dy (and eps(x, y) for a two-output network) at
+ * n points (device [n][2] FP64 in, device [S][n] out in the params' precision,
+ * S = 3 or 4). */
 int fv_mlp_eval(fv_ctx ctx, const fv_mlp_desc* mlp, const void* params_dev, fv_precision prec, int n,
                 const double* xy_dev, void* out_dev);
 

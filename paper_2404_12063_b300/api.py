@@ -249,10 +249,11 @@ class Problem:
         return out, grad
 
     def intermediates(self, params: torch.Tensor):
-        """(out, U [3][P_tot], UB [3][P_tot], R [n_e][T*T]) of one evaluation."""
+        """(out, U [S][P_tot], UB [S][P_tot], R [n_e][T*T]) of one evaluation; S = 3,
+        or 4 for a two-output network (eps(x, y) and its seed last)."""
         self._check_params(params)
         P_tot = self.mesh.n_points + (self.bc.n_bd + self.bc.n_s if self.bc else 0)
-        U = torch.empty(3, P_tot, dtype=self.dtype, device=params.device)
+        U = torch.empty(2 + self.net.widths[-1], P_tot, dtype=self.dtype, device=params.device)
         UB = torch.empty_like(U)
         R = torch.empty(self.mesh.n_elements, self.mesh.Nt, dtype=torch.float64, device=params.device)
         out = torch.zeros(5, dtype=torch.float64, device=params.device)
@@ -330,11 +331,11 @@ class Adam:
 
 
 def mlp_eval(ctx: Context, widths, params: torch.Tensor, xy: torch.Tensor, precision=None) -> torch.Tensor:
-    """(u, u_x, u_y) of the network at device points xy [n][2] (FP64)."""
+    """(u, u_x, u_y[, eps]) of the network at device points xy [n][2] (FP64)."""
     net = Network(widths)
     prec = _prec(precision) if precision is not None else (N.FV_FP64 if params.dtype == torch.float64 else N.FV_FP32)
     xy = xy.to(torch.float64).contiguous()
-    out = torch.empty(3, xy.shape[0], dtype=params.dtype, device=params.device)
+    out = torch.empty(2 + int(widths[-1]), xy.shape[0], dtype=params.dtype, device=params.device)
     N.call("fv_mlp_eval", ctx.h, C.byref(net.desc), _ptr(params), prec, xy.shape[0], _ptr(xy), _ptr(out))
     return out
 

@@ -56,7 +56,7 @@ void clear_error() { g_err[0] = 0; }
 
 bool make_shape(const fv_mlp_desc* d, MlpShape* s) {
   if (!d || !d->widths || d->n_layers < 2 || d->n_layers > kMaxLayers) return false;
-  if (d->widths[0] != 2 || d->widths[d->n_layers] != 1) return false;
+  if (d->widths[0] != 2 || (d->widths[d->n_layers] != 1 && d->widths[d->n_layers] != 2)) return false;
   s->L = d->n_layers;
   int o = 0;
   for (int i = 0; i <= d->n_layers; ++i) {
@@ -250,7 +250,7 @@ int check_eval(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_
   FV_CHECK_ARG(mesh->ctx == ctx && (!bc || bc->ctx == ctx), "evaluation: handles belong to another context");
   FV_CHECK_ARG(opts->norm == FV_NORM_TEST || opts->norm == FV_NORM_ELEM, "evaluation: bad norm");
   if (!make_shape(mlp, sh)) {
-    set_error("network shape unsupported: need widths[0]=2, widths[L]=1, 2..%d affine maps, hidden widths 1..%d",
+    set_error("network shape unsupported: need widths[0]=2, widths[L]=1 or 2, 2..%d affine maps, hidden widths 1..%d",
               kMaxLayers, kMaxWidth);
     return FV_ERR_UNSUPPORTED;
   }
@@ -309,7 +309,8 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   const size_t rsz = pl.prec == FV_FP64 ? 8 : 4;
   int cgrid, E, S;
   size_t csmem;
-  contract_grid(ctx, mesh, pl.prec, &cgrid, &E, &S, &csmem);
+  const int n_str = sh.w[sh.L] == 2 ? 4 : 3;        // value streams: u, u_x, u_y (, eps(x, y))
+  contract_grid(ctx, mesh, pl.prec, &cgrid, &E, &S, &csmem, n_str == 4);
   int nb = 0;
   if (want_grad) {
     nb = tc ? mlp_bwd_tc_blocks(ctx, pl) : mlp_bwd_blocks(ctx, pl);
@@ -317,8 +318,8 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   }
   WsLayout w;
   size_t o = 0;
-  w.U = o; o += al(3 * pl.P_tot * rsz);
-  w.UB = o; o += want_grad ? al(3 * pl.P_tot * rsz) : 0;
+  w.U = o; o += al(n_str * pl.P_tot * rsz);
+  w.UB = o; o += want_grad ? al(n_str * pl.P_tot * rsz) : 0;
   w.cpart = o; o += al(2 * (size_t)cgrid * 8);
   w.bcpart = o; o += al(2 * 8);
   w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
@@ -355,6 +356,9 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   rc = launch_contract(ctx, mesh, forcing, pl, U, UB, opts->eps, eps_dev ? eps_dev : opts->eps_dev, opts->bx, opts->by,
                        2.0 * inv_norm, cpart, &ncp, R_out);
   if (rc) return rc;
+  if (n_str == 4 && UB && pl.P_tot > pl.P_mesh)       // boundary and sensor points: no eps(x, y) seed
+    FV_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(UB) + (3 * pl.P_tot + pl.P_mesh) * rsz, 0,
+                                (pl.P_tot - pl.P_mesh) * rsz, ctx->stream));
   if (bc && pl.n_bd + pl.n_s > 0) {
     cudaEvent_t ta;
     time_begin(ctx, K_BC, &ta);
@@ -369,9 +373,9 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   } else {
     FV_CUDA_TRY(cudaMemsetAsync(bcpart, 0, 16, ctx->stream));
   }
-  if (U_copy) FV_CUDA_TRY(cudaMemcpyAsync(U_copy, U, 3 * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (U_copy) FV_CUDA_TRY(cudaMemcpyAsync(U_copy, U, n_str * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
   if (UB_copy && UB)
-    FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, 3 * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
+    FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, n_str * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
   int ngp = 0;
   if (want_grad && pl.prec == FV_FP16) {
     cudaEvent_t ts;

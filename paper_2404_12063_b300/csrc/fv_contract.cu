@@ -662,8 +662,9 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
 
 }  // namespace
 
-int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, int* stages, size_t* smem) {
-  if (m->g_mode == FV_G_MATRIX_FREE) {
+int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, int* stages, size_t* smem,
+                  bool matrix_free) {
+  if (matrix_free || m->g_mode == FV_G_MATRIX_FREE) {
     int wpb;
     mfree_grid(ctx, m, prec, grid, &wpb, smem);
     *eg = 0; *stages = 0;
@@ -685,6 +686,9 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
   EvalPlan pl;
   pl.prec = prec;
   pl.P_mesh = pl.P_tot = m->P;
+  pl.shape.L = 1;                       // a one-output network: scalar eps
+  pl.shape.w[0] = 2;
+  pl.shape.w[1] = 1;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t u_bytes = 3 * (size_t)m->P * rsz, nf = (size_t)m->n_e * m->Nt;
   const size_t o_ub = al(u_bytes), o_f = o_ub + al(u_bytes), o_f32 = o_f + al(nf * 8), o_part = o_f32 + al(nf * 4);
@@ -747,7 +751,8 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
 int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, const void* U, void* UB, double eps,
                     const double* eps_dev, double bx, double by, double rscale, double* partials, int* n_part,
                     double* R_out) {
-  if (m->g_mode == FV_G_MATRIX_FREE)
+  // eps(x, y) from a two-output network (Sec. 4.7.2) needs the per-node form of the matrix-free kernel
+  if (m->g_mode == FV_G_MATRIX_FREE || pl.shape.w[pl.shape.L] == 2)
     return launch_contract_mfree(ctx, m, f, pl, U, UB, eps, eps_dev, bx, by, rscale, partials, n_part, R_out);
   const ContractPlan P = plan_contract(ctx, m, pl.prec);
   ContractArgs a;

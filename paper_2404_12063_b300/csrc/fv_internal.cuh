@@ -48,10 +48,10 @@ enum KernelKind {
 
 // Network shape passed to kernels by value.
 struct MlpShape {
-  int L;                        // affine maps
-  int w[kMaxLayers + 1];        // widths
-  int off[kMaxLayers];          // flat offset of W_i (b_i follows at off + w[i+1]*w[i])
-  int n_params;
+  int L = 0;                    // affine maps
+  int w[kMaxLayers + 1] = {};   // widths
+  int off[kMaxLayers] = {};     // flat offset of W_i (b_i follows at off + w[i+1]*w[i])
+  int n_params = 0;
 };
 
 bool make_shape(const fv_mlp_desc* d, MlpShape* s);
@@ -225,7 +225,7 @@ int launch_contract(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan
                     double eps, const double* eps_dev, double bx, double by, double rscale, double* partials,
                     int* n_partials_out, double* R_out = nullptr);
 int contract_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* elems_per_stage, int* stages,
-                  size_t* smem);
+                  size_t* smem, bool matrix_free = false);
 int launch_bc(fv_ctx ctx, fv_bc bc, const EvalPlan& pl, const void* U, void* UB, double* partial2);
 int launch_mlp_bwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
                    const void* UB, double* gpart, int* n_blocks_out);

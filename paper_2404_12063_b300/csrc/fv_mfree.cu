@@ -48,8 +48,9 @@ struct MfArgs {
   double* R_out;            // optional [n_e][T*T]
 };
 
-// One element's inputs staged in shared memory: u_x, u_y at its nodes and its F row.
-__host__ __device__ inline int mf_stage_values(int Q, int T) { return ((2 * Q * Q + T * T) + 1) & ~1; }
+// One element's inputs staged in shared memory: u_x, u_y (and eps(x, y)) at its
+// nodes and its F row.
+__host__ __device__ inline int mf_stage_values(int Q, int T) { return ((3 * Q * Q + T * T) + 1) & ~1; }
 // Shared memory per warp (values of R): P, Qm(, C) over the Q x Q nodes, the
 // half-contracted T x Q arrays T1, T2(, T3), the Rbar rows and two input stages.
 __host__ __device__ inline int mf_warp_values(int Q, int T, int nc) {
@@ -57,7 +58,10 @@ __host__ __device__ inline int mf_warp_values(int Q, int T, int nc) {
 }
 __host__ __device__ inline int mf_table_values(int Q, int T) { return 2 * Q + 2 * T * Q; }
 
-template <class R, int NC>
+// EPSQ: eps(x, y) at every node (the second output of a two-output network,
+// Sec. 4.7.2) instead of the scalar eps; the kernel then also writes the seed
+// dL/deps(x_q) = u_x sum_j Rbar_j Gx[j][q] + u_y sum_j Rbar_j Gy[j][q].
+template <class R, int NC, bool EPSQ>
 __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Q = a.Q, T = a.T, Nq = Q * Q, Nt = T * T, TQ = T * Q;
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   R* T2 = T1 + TQ;
   R* T3 = T2 + TQ;                             // NC == 3
   R* Rb = T1 + (NC == 3 ? 3 : 2) * TQ;
-  R* stage = Rb + Nt;                          // [2][u_x (Nq), u_y (Nq), F (Nt)]
+  R* stage = Rb + Nt;                          // [2][u_x (Nq), u_y (Nq), F (Nt), eps (Nq)]
   const int SV = mf_stage_values(Q, T);
 
   const R eps = (R)(a.eps_d ? *a.eps_d : a.eps_h);
@@ -94,6 +98,8 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
         cp_async_val(st + Nq + q, U + 2 * a.P_tot + p0 + q);
       }
       for (int j = lane; j < Nt; j += 32) cp_async_val(st + 2 * Nq + j, F + (size_t)e * Nt + j);
+      if (EPSQ)
+        for (int q = lane; q < Nq; q += 32) cp_async_val(st + 2 * Nq + Nt + q, U + 3 * a.P_tot + p0 + q);
     }
     cp_async_commit();
   };
@@ -126,8 +132,9 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
       const R x_xi = x1 + x3 * t, x_eta = x2 + x3 * s, y_xi = y1 + y3 * t, y_eta = y2 + y3 * s;
       const R w = wq[ia] * wq[ib];
       const R ux = st[q], uy = st[Nq + q];
-      P[q] = w * (y_eta * ux - x_eta * uy);
-      Qm[q] = w * (x_xi * uy - y_xi * ux);
+      const R we = EPSQ ? w * st[2 * Nq + Nt + q] : w;      // eps(x_q) folded into the diffusion terms
+      P[q] = we * (y_eta * ux - x_eta * uy);
+      Qm[q] = we * (x_xi * uy - y_xi * ux);
       if (NC == 3) C[q] = w * (x_xi * y_eta - x_eta * y_xi) * (bx * ux + by * uy);
     }
     __syncwarp();
@@ -155,11 +162,11 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
         A += T1[m * Q + ib] * v[n * Q + ib] + T2[m * Q + ib] * dv[n * Q + ib];
         if (NC == 3) B += T3[m * Q + ib] * v[n * Q + ib];
       }
-      const R Rv = eps * A + B - st[2 * Nq + j];
+      const R Rv = (EPSQ ? A : eps * A) + B - st[2 * Nq + j];
       const R rb = rscale * Rv;
       Rb[j] = rb;
       lsum.add(Rv * Rv);
-      dsum.add(rb * A);
+      if (!EPSQ) dsum.add(rb * A);
       if (a.R_out) a.R_out[(size_t)e * Nt + j] = (double)Rv;
     }
     __syncwarp();
@@ -193,9 +200,11 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
         const R gx = w * (y_eta * sxi - y_xi * seta);          // sum_j Rbar_j Gx[j][q]
         const R gy = w * (x_xi * seta - x_eta * sxi);          // sum_j Rbar_j Gy[j][q]
         const R gv = NC == 3 ? w * (x_xi * y_eta - x_eta * y_xi) * sv : (R)0;
+        const R eq = EPSQ ? st[2 * Nq + Nt + q] : eps;
         UB[p0 + q] = (R)0;
-        UB[a.P_tot + p0 + q] = eps * gx + bx * gv;
-        UB[2 * a.P_tot + p0 + q] = eps * gy + by * gv;
+        UB[a.P_tot + p0 + q] = eq * gx + bx * gv;
+        UB[2 * a.P_tot + p0 + q] = eq * gy + by * gv;
+        if (EPSQ) UB[3 * a.P_tot + p0 + q] = st[q] * gx + st[Nq + q] * gy;
       }
     }
     __syncwarp();
@@ -225,18 +234,22 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   }
 }
 
-template <class R, int NC>
+template <class R, int NC, bool EPSQ>
 cudaError_t launch_mf(fv_ctx ctx, const MfArgs& a, int grid, int wpb, size_t smem) {
-  cudaError_t e = ensure_smem_attr(ctx, (const void*)contract_mfree<R, NC>, smem);
-  if (e == cudaSuccess) contract_mfree<R, NC><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
+  cudaError_t e = ensure_smem_attr(ctx, (const void*)contract_mfree<R, NC, EPSQ>, smem);
+  if (e == cudaSuccess) contract_mfree<R, NC, EPSQ><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
   return e;
+}
+template <class R, bool EPSQ>
+cudaError_t launch_mf_nc(fv_ctx ctx, const MfArgs& a, int nc, int grid, int wpb, size_t smem) {
+  return nc == 3 ? launch_mf<R, 3, EPSQ>(ctx, a, grid, wpb, smem) : launch_mf<R, 2, EPSQ>(ctx, a, grid, wpb, smem);
 }
 
 }  // namespace
 
 template <class R, int NC>
 int mf_blocks_per_sm(fv_ctx ctx, int wpb, size_t smem) {
-  return std::max(1, occupancy(ctx, (const void*)contract_mfree<R, NC>, 32 * wpb, smem));
+  return std::max(1, occupancy(ctx, (const void*)contract_mfree<R, NC, true>, 32 * wpb, smem));
 }
 
 // Warps per CTA (up to 8) such that tables and per-warp scratch fit in about
@@ -282,10 +295,13 @@ int launch_contract_mfree(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& p
   cudaEvent_t ta;
   time_begin(ctx, K_CONTRACT, &ta);
   cudaError_t e;
+  const bool epsq = pl.shape.w[pl.shape.L] == 2;
   if (pl.prec == FV_FP64)
-    e = m->n_comp == 3 ? launch_mf<double, 3>(ctx, a, grid, wpb, smem) : launch_mf<double, 2>(ctx, a, grid, wpb, smem);
+    e = epsq ? launch_mf_nc<double, true>(ctx, a, m->n_comp, grid, wpb, smem)
+             : launch_mf_nc<double, false>(ctx, a, m->n_comp, grid, wpb, smem);
   else
-    e = m->n_comp == 3 ? launch_mf<float, 3>(ctx, a, grid, wpb, smem) : launch_mf<float, 2>(ctx, a, grid, wpb, smem);
+    e = epsq ? launch_mf_nc<float, true>(ctx, a, m->n_comp, grid, wpb, smem)
+             : launch_mf_nc<float, false>(ctx, a, m->n_comp, grid, wpb, smem);
   if (e == cudaSuccess) e = cudaGetLastError();
   time_end(ctx, K_CONTRACT, ta);
   if (e != cudaSuccess) {

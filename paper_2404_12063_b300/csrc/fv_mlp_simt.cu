@@ -255,19 +255,24 @@ __global__ void __launch_bounds__(kThreads) mlp_fwd_simt(FwdArgs a) {
     const R* Wl = sW + wl.woff[L - 1];
     const R bl = sW[wl.boff[L - 1]];
     const int in = sh.w[L - 1];
+    const bool two = sh.w[L] == 2;                 // second output eps(x, y) (Sec. 4.7.2)
+    const R* We = Wl + wl.ld[L - 1];
+    const R be = sW[wl.boff[L - 1] + 1];
     for (int p = threadIdx.x; p < a.TP; p += blockDim.x) {
       const int64_t gp = p_base + p;
       if (gp >= a.P_tot) continue;
-      R u = bl, ux = 0, uy = 0;
+      R u = bl, ux = 0, uy = 0, e = be;
       for (int k = 0; k < in; ++k) {
         const R w = Wl[k];
         u = fma(w, A[k * a.TPS + p], u);
         ux = fma(w, A[plane + k * a.TPS + p], ux);
         uy = fma(w, A[2 * plane + k * a.TPS + p], uy);
+        if (two) e = fma(We[k], A[k * a.TPS + p], e);
       }
       U[gp] = u;
       U[a.P_tot + gp] = ux;
       U[2 * a.P_tot + gp] = uy;
+      if (two) U[3 * a.P_tot + gp] = e;
     }
   }
 }
@@ -402,7 +407,8 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
   R* Zb = S + (size_t)(L - 1) * 3 * plane;
   R* Tb = Zb + 3 * plane;
   R* sX = Tb + 3 * plane;                                         // [2][TPS]
-  R* sSeed = sX + 2 * TPS;                                        // [3][TPS]
+  R* sSeed = sX + 2 * TPS;                                        // [4][TPS]: u, u_x, u_y (, eps) seeds
+  const bool two = sh.w[L] == 2;
   for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) G.zero(i);
   load_weights<R>(sh, wl, reinterpret_cast<const R*>(a.params), sW);
   const R* UB = reinterpret_cast<const R*>(a.UB);
@@ -417,6 +423,7 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
       sSeed[p] = in ? UB[gp] : (R)0;
       sSeed[TPS + p] = in ? UB[a.P_tot + gp] : (R)0;
       sSeed[2 * TPS + p] = in ? UB[2 * a.P_tot + gp] : (R)0;
+      if (two) sSeed[3 * TPS + p] = in ? UB[3 * a.P_tot + gp] : (R)0;
     }
     __syncthreads();
     // forward recompute, keeping every hidden layer's (t, t'_x, t'_y)
@@ -427,29 +434,39 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
                    S + (size_t)i * 3 * plane, TP, TPS, plane);
       __syncthreads();
     }
-    // output layer: gradient of w_L, b_L and seeds for the last hidden layer
+    // output layer: gradient of w_L, b_L and seeds for the last hidden layer; a
+    // second output eps(x, y) takes a value seed only (it has no tangents)
     {
-      const int in = sh.w[L - 1];
+      const int in = sh.w[L - 1], nout = sh.w[L];
       const R* H = S + (size_t)(L - 2) * 3 * plane;
       const R* Wl = sW + wl.woff[L - 1];
+      const R* We = Wl + wl.ld[L - 1];
       const int goff = sh.off[L - 1];
       for (int k = threadIdx.x; k < in; k += blockDim.x) {
-        R acc = 0;
-        for (int p = 0; p < TP; ++p)
+        R acc = 0, acce = 0;
+        for (int p = 0; p < TP; ++p) {
           acc += sSeed[p] * H[k * TPS + p] + sSeed[TPS + p] * H[plane + k * TPS + p] +
                  sSeed[2 * TPS + p] * H[2 * plane + k * TPS + p];
+          if (two) acce += sSeed[3 * TPS + p] * H[k * TPS + p];
+        }
         G.add(goff + k, acc);
+        if (two) G.add(goff + in + k, acce);
       }
       if (threadIdx.x == 0) {
-        R acc = 0;
-        for (int p = 0; p < TP; ++p) acc += sSeed[p];
-        G.add(goff + in, acc);
+        R acc = 0, acce = 0;
+        for (int p = 0; p < TP; ++p) {
+          acc += sSeed[p];
+          if (two) acce += sSeed[3 * TPS + p];
+        }
+        G.add(goff + nout * in, acc);
+        if (two) G.add(goff + nout * in + 1, acce);
       }
       const int rows = wl.rows[L - 2];
       for (int idx = threadIdx.x; idx < rows * TP; idx += blockDim.x) {
         const int k = idx / TP, p = idx - k * TP;
         const R w = k < in ? Wl[k] : (R)0;
-        Tb[k * TPS + p] = w * sSeed[p];
+        const R we = two && k < in ? We[k] : (R)0;
+        Tb[k * TPS + p] = w * sSeed[p] + (two ? we * sSeed[3 * TPS + p] : (R)0);
         Tb[plane + k * TPS + p] = w * sSeed[TPS + p];
         Tb[2 * plane + k * TPS + p] = w * sSeed[2 * TPS + p];
       }
@@ -484,7 +501,7 @@ size_t fwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rs
 size_t bwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rsz) {
   const int TPS = tps_for(TP);
   size_t b = 8 * (size_t)((sh.n_params + 1) & ~1);
-  b += rsz * ((size_t)wl.total + (size_t)(sh.L - 1) * 3 * DP * TPS + 6 * (size_t)DP * TPS + 5 * TPS);
+  b += rsz * ((size_t)wl.total + (size_t)(sh.L - 1) * 3 * DP * TPS + 6 * (size_t)DP * TPS + 6 * TPS);
   return b;
 }
 

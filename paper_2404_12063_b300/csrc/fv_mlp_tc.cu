@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 1) mlp_bwd_tc(TcArgs a) {
 bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
   const MlpShape& s = ep.shape;
   if (ep.prec != FV_BF16 && ep.prec != FV_FP16) return false;
-  if (s.L < 2) return false;
+  if (s.L < 2 || s.w[s.L] != 1) return false;     // one output (u); eps(x, y) networks run on CUDA cores
   p->L = s.L;
   p->n_params = s.n_params;
   int HP = 16;

@@ -356,6 +356,67 @@ def test_matrix_free_mode_argument_errors(api, ctx):
     assert ei.value.code == N.FV_ERR_ARG
 
 
+# ---------------------------------------------------------------- space-dependent eps (two-output network)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_eps_field_matches_oracle(api, ctx, precision):
+    out, grad, ref = check_against_oracle(api, ctx, fi.config_eps_field(), precision)
+    assert out[4] == 0.0
+
+
+def test_eps_field_intermediates_elementwise(api, ctx):
+    """eps(x_q) and the seeds dL/deps(x_q), dL/du_x, dL/du_y against the oracle, node by node."""
+    mesh = fi.jitter_nodes(fi.rect_grid(3, 2), ~fi.boundary_nodes_of(fi.rect_grid(3, 2)), 0.2, seed=4)
+    widths = [2, 7, 6, 2]
+    u, f = fi.sinsin(2.0)
+    bd = fi.square_boundary_points(4)
+    sens = fi.uniform_points(6, 4, 2, 0, 1)
+    prob = fi.Problem("eps-field-small", mesh, 6, 4, widths, fi.random_bias_params(widths, 3, 1, gain=1.2), u, f,
+                      bd, u(bd[:, 0], bd[:, 1]), eps=9.0, b=(0.7, -0.4), tau=2.0, sensor_xy=sens,
+                      sensor_u=u(sens[:, 0], sens[:, 1]), gamma=3.0)
+    pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp64", intermediates=True)
+    ref = oracle_eval(prob, prob.params, want_R=True, want_ubar=True, want_eps_field=True)
+    P = prob.n_points
+    assert U.shape[0] == 4 and UB.shape[0] == 4
+    assert np.max(np.abs(U[3, :P] - ref["epts"].reshape(-1))) < 1e-12 * np.max(np.abs(ref["epts"]))
+    assert np.max(np.abs(R - ref["R"])) < 1e-11 * np.max(np.abs(ref["R"]))
+    ub = ref["ubar"].reshape(-1, 2)
+    assert np.max(np.abs(UB[1, :P] - ub[:, 0])) < 1e-11 * np.max(np.abs(ub))
+    assert np.max(np.abs(UB[2, :P] - ub[:, 1])) < 1e-11 * np.max(np.abs(ub))
+    eb = ref["ebar"].reshape(-1)
+    assert np.max(np.abs(UB[3, :P] - eb)) < 1e-11 * np.max(np.abs(eb))
+    assert np.all(UB[3, P:] == 0.0)
+    # eps(x, y) at the boundary and sensor points too (the network's second output)
+    e_bd = oracle.mlp_eps(widths, prob.params, np.concatenate([bd, sens]))
+    assert np.max(np.abs(U[3, P:] - e_bd)) < 1e-12 * max(1.0, np.max(np.abs(e_bd)))
+
+
+def test_eps_field_constant_output_equals_scalar_eps(api, ctx):
+    """GPU: a two-output network whose eps row is zero and bias eps0 gives the
+    scalar-eps problem's loss, and its eps-bias gradient is that problem's dL/deps."""
+    prob1 = _with(cfg(1), eps=0.65, b=(0.3, -0.2))
+    n_in = prob1.widths[-2]
+    p1 = prob1.params
+    p2 = np.concatenate([p1[:len(p1) - (n_in + 1)], p1[len(p1) - (n_in + 1): len(p1) - 1], np.zeros(n_in),
+                         [p1[-1], 0.65]])
+    prob2 = _with(prob1, widths=prob1.widths[:-1] + [2], params=p2, eps=42.0)
+    _, _, o1, g1 = gpu_eval(api, ctx, prob1, "fp64")
+    _, _, o2, g2 = gpu_eval(api, ctx, prob2, "fp64")
+    assert rel(o2[0], o1[0]) < 1e-12
+    head = len(p1) - (n_in + 1)
+    assert rel(g2[:head + n_in], g1[:head + n_in]) < 1e-12
+    assert rel(g2[-1], o1[4]) < 1e-11
+
+
+def test_eps_field_rejected_by_tensor_cores(api, ctx):
+    from paper_2404_12063_b300 import FVError, _native as N
+    prob = fi.config_eps_field()
+    pb = api.problem_from_inputs(ctx, prob, "fp16", storage="fp32")
+    params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+    with pytest.raises(FVError) as ei:
+        pb.loss_grad(params)
+    assert ei.value.code == N.FV_ERR_UNSUPPORTED
+
+
 # ---------------------------------------------------------------- bindings, Adam, batches
 def test_autograd_function(api, ctx):
     prob = cfg(1)
