@@ -153,9 +153,19 @@ int fv_mesh_destroy(fv_mesh mesh);
  * rounding (the matrix-free form rounds geometry in the evaluation precision
  * instead of rounding G to the storage precision).  The paper precomputes G
  * (Sec. 4.2); the matrix-free form is this library's extension.
- * Errors: FV_ERR_ARG (null mesh, mode not 0 or 1). */
+ * FV_G_REGULAR: the regular-element form of Alg. 2 (Sec. 4.3, premultipliers
+ * as in the appendix's assembly): every element must be an axis-aligned
+ * rectangle, so its premultipliers are one reference matrix scaled by the
+ * element's Jacobian terms, and a tile of 128 elements' residuals and seeds
+ * are four GEMMs with N = elements on the tensor cores (BF16 / FP16
+ * evaluations, Q*Q and T*T <= 128); other precisions and shapes use the
+ * matrix-free kernel, which computes the same quantities.
+ * Errors: FV_ERR_ARG (null mesh, mode not 0, 1 or 2; FV_G_REGULAR on a mesh
+ * with an element that is not an axis-aligned rectangle, named in the
+ * message), FV_ERR_CUDA. */
 #define FV_G_STORED 0
 #define FV_G_MATRIX_FREE 1
+#define FV_G_REGULAR 2
 int fv_mesh_set_g_mode(fv_mesh mesh, int mode);
 
 /* Autotune the contraction of Alg. 3 for this mesh at evaluation precision

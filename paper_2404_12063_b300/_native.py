@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfastvpinn.so")
 
 FV_OK, FV_ERR_ARG, FV_ERR_DEGENERATE_ELEMENT, FV_ERR_UNSUPPORTED, FV_ERR_OOM, FV_ERR_CUDA, FV_ERR_TIMEOUT = range(7)
 FV_FP64, FV_FP32, FV_TF32, FV_BF16, FV_FP16 = range(5)
-FV_G_STORED, FV_G_MATRIX_FREE = 0, 1
+FV_G_STORED, FV_G_MATRIX_FREE, FV_G_REGULAR = 0, 1, 2
 FV_NORM_TEST, FV_NORM_ELEM = range(2)
 
 ERR_NAMES = {1: "FV_ERR_ARG", 2: "FV_ERR_DEGENERATE_ELEMENT", 3: "FV_ERR_UNSUPPORTED", 4: "FV_ERR_OOM",

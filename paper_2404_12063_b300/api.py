@@ -105,8 +105,10 @@ class Mesh:
 
     def set_g_mode(self, mode: str = "stored"):
         """'stored' streams the stored G tensor; 'matrix_free' rebuilds it in
-        the contraction from the element vertices (fv_mesh_set_g_mode)."""
-        m = {"stored": N.FV_G_STORED, "matrix_free": N.FV_G_MATRIX_FREE}[mode]
+        the contraction from the element vertices; 'regular' (axis-aligned
+        rectangles only) runs Alg. 2's reference-matrix GEMMs on the tensor
+        cores (fv_mesh_set_g_mode)."""
+        m = {"stored": N.FV_G_STORED, "matrix_free": N.FV_G_MATRIX_FREE, "regular": N.FV_G_REGULAR}[mode]
         N.call("fv_mesh_set_g_mode", self.h, m)
         self.g_mode = mode
 

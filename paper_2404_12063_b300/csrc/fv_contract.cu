@@ -664,7 +664,12 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
 
 int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, int* stages, size_t* smem,
                   bool matrix_free) {
-  if (matrix_free || m->g_mode == FV_G_MATRIX_FREE) {
+  if (!matrix_free && m->g_mode == FV_G_REGULAR && regular_supported(m, prec)) {
+    *grid = regular_grid(ctx, m);
+    *eg = 0; *stages = 0; *smem = 0;
+    return FV_OK;
+  }
+  if (matrix_free || m->g_mode != FV_G_STORED) {
     int wpb;
     mfree_grid(ctx, m, prec, grid, &wpb, smem);
     *eg = 0; *stages = 0;
@@ -752,7 +757,11 @@ int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, con
                     const double* eps_dev, double bx, double by, double rscale, double* partials, int* n_part,
                     double* R_out) {
   // eps(x, y) from a two-output network (Sec. 4.7.2) needs the per-node form of the matrix-free kernel
-  if (m->g_mode == FV_G_MATRIX_FREE || pl.shape.w[pl.shape.L] == 2)
+  const bool eps_field = pl.shape.w[pl.shape.L] == 2;
+  // regular meshes (Alg. 2): tensor-core GEMMs in the 16-bit forms, otherwise the matrix-free kernel
+  if (m->g_mode == FV_G_REGULAR && !eps_field && regular_supported(m, pl.prec))
+    return launch_contract_regular(ctx, m, f, pl, U, UB, eps, eps_dev, bx, by, rscale, partials, n_part, R_out);
+  if (m->g_mode != FV_G_STORED || eps_field)
     return launch_contract_mfree(ctx, m, f, pl, U, UB, eps, eps_dev, bx, by, rscale, partials, n_part, R_out);
   const ContractPlan P = plan_contract(ctx, m, pl.prec);
   ContractArgs a;

@@ -221,6 +221,12 @@ int launch_contract_mfree(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const Ev
                           void* UB, double eps, const double* eps_dev, double bx, double by, double rscale,
                           double* partials, int* n_partials_out, double* R_out);
 void mfree_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* warps_per_cta, size_t* smem);
+bool regular_supported(fv_mesh mesh, fv_precision prec);
+int regular_grid(fv_ctx ctx, fv_mesh mesh);
+int check_regular_mesh(fv_mesh mesh);
+int launch_contract_regular(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U,
+                            void* UB, double eps, const double* eps_dev, double bx, double by, double rscale,
+                            double* partials, int* n_partials_out, double* R_out);
 int launch_contract(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U, void* UB,
                     double eps, const double* eps_dev, double bx, double by, double rscale, double* partials,
                     int* n_partials_out, double* R_out = nullptr);

@@ -313,7 +313,13 @@ extern "C" int fv_mesh_destroy(fv_mesh m) {
 extern "C" int fv_mesh_set_g_mode(fv_mesh m, int mode) {
   clear_error();
   FV_CHECK_ARG(m, "fv_mesh_set_g_mode: null mesh");
-  FV_CHECK_ARG(mode == FV_G_STORED || mode == FV_G_MATRIX_FREE, "fv_mesh_set_g_mode: mode %d is not 0 or 1", mode);
+  FV_CHECK_ARG(mode == FV_G_STORED || mode == FV_G_MATRIX_FREE || mode == FV_G_REGULAR,
+               "fv_mesh_set_g_mode: mode %d is not 0, 1 or 2", mode);
+  if (mode == FV_G_REGULAR) {
+    FV_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    const int rc = check_regular_mesh(m);
+    if (rc) return rc;
+  }
   m->g_mode = mode;
   return FV_OK;
 }

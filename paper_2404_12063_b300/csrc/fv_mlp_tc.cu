@@ -22,139 +22,20 @@
 #include <algorithm>
 
 #include "fv_internal.cuh"
+#include "fv_tcgen05.cuh"
 
 namespace fv {
 namespace {
+
+using namespace fv::tc;
 
 constexpr int kTile = 128;
 // 128 x (HP/16) threads: thread (quarter q, group g, lane l) owns point
 // p = 32 q + l (TMEM lane p) and the 16 columns [16 g, 16 g + 16).
 template <int HP> constexpr int tc_threads() { return kTile * (HP / 16); }
-constexpr uint64_t kTcWaitNs = 2000000000ull;
 
 inline int ru16(int v) { return (v + 15) & ~15; }
 
-// ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (gtimer() - t0 > kTcWaitNs) return false;
-  }
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, no swizzle: start, LBO (K-direction core
-// matrix stride), SBO (M/N-direction 8-row group stride), version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-// Instruction descriptor, kind::f16: D F32, A/B format fmt (0 F16, 1 BF16), majors, N, M.
-__device__ __forceinline__ uint32_t idesc_f16(uint32_t fmt, int M, int N, int a_mn, int b_mn) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// 16-bit operand formats for kind::f16: BF16 (8-bit significand, FP32 range)
-// or FP16 (11-bit significand; the reverse sweep scales its adjoints by a
-// power of two to stay inside FP16's range).
-struct OpBF16 {
-  static constexpr uint32_t fmt = 1;
-  __device__ static __forceinline__ uint32_t pack(float lo, float hi) {
-    uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-  }
-  __device__ static __forceinline__ float lo(uint32_t u) { return __uint_as_float(u << 16); }
-  __device__ static __forceinline__ float hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
-};
-struct OpF16 {
-  static constexpr uint32_t fmt = 0;
-  __device__ static __forceinline__ uint32_t pack(float lo, float hi) {
-    uint32_t r;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-  }
-  __device__ static __forceinline__ float lo(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu))); }
-  __device__ static __forceinline__ float hi(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)(u >> 16))); }
-};
-
-__device__ __forceinline__ float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Activation tile layout (one stream): row p, column k of a [128 x Kb] BF16
-// tile: (p/8)*Kb*16 + (k/8)*128 + (p%8)*16 + (k%8)*2 bytes.  A stream spans
-// 256*Kb bytes.
-__device__ __forceinline__ uint32_t row_off(int p, int Kb) { return (p >> 3) * (Kb * 16) + (p & 7) * 16; }
-
-// 8 columns [c, c+8) of row p (one 16-byte core-matrix row segment).
-__device__ __forceinline__ void st8(uint8_t* stream, int Kb, int p, int c, const uint32_t pk[4]) {
-  *reinterpret_cast<uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-}
-template <class OP>
-__device__ __forceinline__ void ld8(const uint8_t* stream, int Kb, int p, int c, float v[8]) {
-  const uint4 x = *reinterpret_cast<const uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128);
-  const uint32_t u[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) { v[2 * i] = OP::lo(u[i]); v[2 * i + 1] = OP::hi(u[i]); }
-}
 // ------------------------------------------------------------------ plan
 struct TcPlan {
   int L;

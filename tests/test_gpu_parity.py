@@ -356,6 +356,46 @@ def test_matrix_free_mode_argument_errors(api, ctx):
     assert ei.value.code == N.FV_ERR_ARG
 
 
+# ---------------------------------------------------------------- regular-mesh path (Alg. 2)
+def _uniform_problem(nx, ny, Q, T, b=(0.0, 0.0), eps=1.0, seed=7):
+    mesh = fi.rect_grid(nx, ny, 0.0, 1.0, 0.0, 0.7)
+    u, f = fi.sinsin(2 * math.pi)
+    widths = [2, 30, 30, 30, 1]
+    bd = fi.square_boundary_points(40, 0, 1, 0, 0.7)
+    return fi.Problem("uniform", mesh, Q, T, widths, fi.glorot_params(widths, seed, 1), u, f, bd,
+                      u(bd[:, 0], bd[:, 1]), eps=eps, b=b, tau=3.0)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+@pytest.mark.parametrize("nx,ny,Q,T,b,eps", [(4, 4, 5, 5, (0.0, 0.0), 1.0), (15, 20, 10, 8, (0.4, -0.3), 0.8),
+                                             (3, 5, 11, 11, (0.2, 0.1), 1.3), (1, 1, 3, 2, (0.0, 0.0), 1.0)])
+def test_regular_mesh_matches_oracle(api, ctx, precision, nx, ny, Q, T, b, eps):
+    """Alg. 2's reference-matrix GEMMs on the tensor cores (ragged element
+    tiles, convection, eps != 1, the largest supported orders)."""
+    prob = _uniform_problem(nx, ny, Q, T, b, eps)
+    check_against_oracle(api, ctx, prob, precision, g_mode="regular")
+
+
+def test_regular_mesh_agrees_with_stored_g(api, ctx):
+    prob = _uniform_problem(15, 20, 10, 8, (0.4, -0.3), 0.8)
+    _, _, o_r, g_r = gpu_eval(api, ctx, prob, "fp16", g_mode="regular")
+    _, _, o_s, g_s = gpu_eval(api, ctx, prob, "fp16", storage="fp32")
+    assert rel(o_r[0], o_s[0]) < 5e-3
+    assert rel(g_r, g_s) < 5e-3
+
+
+def test_regular_mode_rejects_a_skewed_mesh(api, ctx):
+    from paper_2404_12063_b300 import FVError, _native as N
+    pb = api.problem_from_inputs(ctx, cfg(2), "fp16")
+    with pytest.raises(FVError) as ei:
+        pb.mesh.set_g_mode("regular")
+    assert ei.value.code == N.FV_ERR_ARG and "axis-aligned" in str(ei.value)
+
+
+def test_regular_mode_fp32_uses_the_matrix_free_kernel(api, ctx):
+    check_against_oracle(api, ctx, _uniform_problem(6, 5, 7, 5, (0.3, 0.0), 0.9), "fp32", g_mode="regular")
+
+
 # ---------------------------------------------------------------- space-dependent eps (two-output network)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_eps_field_matches_oracle(api, ctx, precision):
