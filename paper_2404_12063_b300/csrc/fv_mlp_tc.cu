@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
 
 // ------------------------------------------------------------------ reverse kernel
 template <int HP, class OP>
-__global__ void __launch_bounds__(tc_threads<HP>(), 1) mlp_bwd_tc(TcArgs a) {
+__global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc(TcArgs a) {
   constexpr int NT = tc_threads<HP>();
   extern __shared__ __align__(1024) uint8_t sm[];
   const TcPlan& pl = a.pl;
