@@ -314,6 +314,60 @@ def run_ablation(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- contraction forms
+def run_forms(args):
+    """The three contraction forms on uniform grids (where all three apply), FP16 network:
+    stored G (BF16, autotuned plan), matrix-free (sum factorisation), and the regular-mesh
+    reference-matrix GEMMs of Alg. 2 on the tensor cores.  Median per-launch time of the
+    contraction over `steps` evaluations (CUDA events around the launch)."""
+    import torch
+    import fv_inputs as fi
+    from paper_2404_12063_b300 import api
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(local, stream)
+    u, f = fi.sinsin(2 * math.pi)
+    widths = [2, 30, 30, 30, 1]
+    bd = fi.square_boundary_points(100)
+    steps = max(5, min(args.steps, 50))
+    rows = []
+    for (nx, Q, T) in ((128, 10, 8), (256, 10, 8), (256, 5, 5), (128, 8, 6)):
+        prob = fi.Problem("uniform", fi.rect_grid(nx, nx), Q, T, widths, fi.glorot_params(widths, 1, 1), u, f, bd,
+                          u(bd[:, 0], bd[:, 1]))
+        row = {"elements": nx * nx, "Q": Q, "T": T}
+        for name, mode, st in (("stored_bf16_G", None, "bf16"), ("matrix_free", "matrix_free", "fp32"),
+                               ("regular_tensor_core", "regular", "fp32")):
+            pb = api.problem_from_inputs(ctx, prob, "fp16", storage=st, g_mode=mode)
+            if mode is None:
+                pb.mesh.autotune("fp16")
+            params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+            for _ in range(max(3, args.warmup)):
+                pb.loss_grad(params)
+            torch.cuda.synchronize()
+            ctx.reset_kernel_times()
+            ctx.enable_timing(True)
+            ts = []
+            for _ in range(steps):
+                pb.loss_grad(params)
+                torch.cuda.synchronize()
+                kt = ctx.kernel_times()
+                ts.append(kt["contract"][0])
+                ctx.reset_kernel_times()
+            ctx.enable_timing(False)
+            row[name + "_us"] = 1e3 * statistics.median(ts)
+            del pb
+        rows.append(row)
+    line = {"metric": "contraction time per launch, three forms on uniform grids", "unit": "us",
+            "value": rows[1]["matrix_free_us"], "higher_is_better": False, "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "dtype": "f16/f32-accum", "data": "synthetic",
+            "config": {"workload": "uniform unit-square grids", "mlp": "2-30x3-1"}, "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- batch workload
 def run_batch(args):
     """64 independent Poisson instances (uniform grids, N_e log-uniform in
@@ -398,7 +452,7 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="annulus", choices=["annulus", "batch", "ablation"])
+    ap.add_argument("--workload", default="annulus", choices=["annulus", "batch", "ablation", "forms"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -407,6 +461,8 @@ def main():
         return run_batch(args)
     if args.workload == "ablation":
         return run_ablation(args)
+    if args.workload == "forms":
+        return run_forms(args)
     prob = fi.config3_annulus()
     if args.impl == "reference":
         return run_reference(args, prob)
