@@ -112,10 +112,20 @@ __device__ void tc_load_weights(const TcPlan& pl, const float* __restrict__ P, u
   if (threadIdx.x == 0) s[4 * HP] = P[pl.off[L - 1] + pl.w[L - 1]];
 }
 
-__device__ __forceinline__ void point_xy(const TcArgs& a, int64_t gp, float& x, float& y) {
-  x = 0.f; y = 0.f;
-  if (gp < a.P_mesh) { x = (float)a.Xm[2 * gp]; y = (float)a.Xm[2 * gp + 1]; }
-  else if (gp < a.P_tot) { x = (float)a.Xe[2 * (gp - a.P_mesh)]; y = (float)a.Xe[2 * (gp - a.P_mesh) + 1]; }
+// A point's coordinates and (reverse sweep) seeds as loaded from global memory;
+// zero past the end.
+struct PointIn {
+  double x, y;
+  float s[3];
+};
+
+__device__ __forceinline__ void point_fetch(const TcArgs& a, int64_t gp, PointIn& in) {
+  in.x = 0.0; in.y = 0.0;
+  if (gp < a.P_mesh) { in.x = a.Xm[2 * gp]; in.y = a.Xm[2 * gp + 1]; }
+  else if (gp < a.P_tot) { in.x = a.Xe[2 * (gp - a.P_mesh)]; in.y = a.Xe[2 * (gp - a.P_mesh) + 1]; }
+  const bool live = gp < a.P_tot && a.UB;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) in.s[k] = live ? a.UB[k * a.P_tot + gp] : 0.f;
 }
 
 // Layer 0 on CUDA cores: H_0 row p (3 streams), this thread's 16 columns.
@@ -152,8 +162,7 @@ __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_sm
 
 // MMAs into one accumulator run as a dependent chain; MMAs into independent
 // accumulators overlap in the tensor pipe.  So the three streams' MMAs are
-// issued round-robin (K step outer, stream inner), and the reverse step
-// interleaves its adjoint-product MMAs into the weight-gradient chain.
+// issued round-robin (K step outer, stream inner).
 
 // Forward MMAs of map i: D_s (columns s*HP) = H_{i-1,s} W_i^T, K = Kin, N = Nout.
 __device__ __forceinline__ void issue_fwd(uint32_t fmt, uint32_t tD, uint32_t abuf, uint32_t wbuf, int Kin, int Nout,
@@ -168,7 +177,8 @@ __device__ __forceinline__ void issue_fwd(uint32_t fmt, uint32_t tD, uint32_t ab
 }
 
 // Reverse step of map i >= 1 (all weight-gradient MMAs, then all adjoint
-// products: mixing the two shapes in the issue order slows the pipe):
+// products, one commit: issuing the adjoint products first with a commit of
+// their own, or mixing the two shapes in the issue order, slows the pipe):
 //   Wbar_i (M = 64 rows o, N = Kin) += sum over streams and points of Zbar^T B,
 //     both read MN-major; K runs over 3 streams x 128 points (one chain);
 //   Tbar_s (columns s*HP) = Zbar_s W_i: A = Zbar (K-major, K = Nout), B = W_i
@@ -236,10 +246,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
   bool failed = false;
   const int L = pl.L;
   const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
+  PointIn nxt;                                  // next tile's coordinates, loads in flight
+  if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     const int64_t gp = tile * kTile + p;
-    float x, y;
-    point_xy(a, gp, x, y);
+    const float x = (float)nxt.x, y = (float)nxt.y;
+    if (tile + gridDim.x < n_tiles) point_fetch(a, (tile + gridDim.x) * kTile + p, nxt);
     float u = 0.f, ux = 0.f, uy = 0.f;          // output-layer partial sums over this thread's columns
     if (L == 2) {   // one hidden layer: output straight from layer 0
       for (int o = c0; o < min(pl.w[1], c0 + 16); ++o) {
@@ -450,21 +462,17 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     return true;
   };
 
-  // this thread's point inputs for a tile: coordinates and (scaled) seeds
-  auto fetch = [&](int64_t tile, float (&in)[5]) {
-    const int64_t gp = tile * kTile + p;
-    point_xy(a, gp, in[0], in[1]);
-    const bool live = gp < a.P_tot;
-    in[2] = live ? sc * a.UB[gp] : 0.f;
-    in[3] = live ? sc * a.UB[a.P_tot + gp] : 0.f;
-    in[4] = live ? sc * a.UB[2 * a.P_tot + gp] : 0.f;
-  };
+  // this thread's point inputs for a tile (coordinates and seeds), kept as
+  // loaded so that the loads of the next tile stay in flight until first use
   const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
-  float nxt[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  if (blockIdx.x < n_tiles) fetch(blockIdx.x, nxt);
+  PointIn nxt;
+  if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
+  bool h0_ready = false;           // H_0 of this tile already in buf[0] (computed under the previous tile's MMAs)
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-    const float x = nxt[0], y = nxt[1], su = nxt[2], sx = nxt[3], sy = nxt[4];
-    if (tile + gridDim.x < n_tiles) fetch(tile + gridDim.x, nxt);     // next tile's inputs, in flight meanwhile
+    const float x = (float)nxt.x, y = (float)nxt.y;
+    const float su = sc * nxt.s[0], sx = sc * nxt.s[1], sy = sc * nxt.s[2];
+    const bool has_next = tile + gridDim.x < n_tiles;
+    if (has_next) point_fetch(a, (tile + gridDim.x) * kTile + p, nxt);
     if (grp == 0) {
       uint32_t xr[4] = {OP::pack(x, y), OP::pack(1.f, 0.f), 0, 0};
       st8(xbuf, 16, p, 0, xr);
@@ -475,7 +483,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     //      layer and the seeds and writes Zbar_{L-2} (its H is never stored)
     const int last = L - 2;
     if (last >= 1) {
-      layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+      if (!h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
       publish();
       for (int i = 1; i < last; ++i) {
         issue_fwd_map(i);
@@ -566,6 +574,18 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
           issue_wbar0(OP::fmt, tD + pl.c_wbar[0], su32(zb), pl.WP[0], bsrc, (wfirst >> 0) & 1u);
         wfirst &= ~(1u << i);
         mma_commit(bar);
+      }
+      // CUDA-core work on dead tiles while the tensor core runs: H_0 for map 1's
+      // reverse step into buf[0] (H_2 there is dead once map 3's step is done),
+      // and under map 0's step the next tile's H_0 (buf[0] held this tile's H_0,
+      // read by map 1's step only)
+      if (i == 2 && bufH[0] != 0) {
+        layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+        bufH[0] = 0;
+      }
+      if (i == 0) {
+        h0_ready = last >= 1 && has_next;
+        if (h0_ready) layer0_store<OP>(pl, s_small, (float)nxt.x, (float)nxt.y, p, c0, sm + pl.o_buf[0]);
       }
       if (!sync_mma()) { failed = true; break; }
       if (i >= 1) {
