@@ -413,6 +413,9 @@ def run_batch(args):
     bo, bg = batch.run()
     torch.cuda.synchronize()
     same = all(torch.equal(a[:4], b[:4]) for a, b in zip(bo, outs)) and all(torch.equal(a, b) for a, b in zip(bg, grads))
+    max_rel = max(max(float((a[:4] - b[:4]).abs().max() / b[:4].abs().max().clamp_min(1e-300)) for a, b in zip(bo, outs)),
+                  max(float((a.double() - b.double()).abs().max() / b.double().abs().max().clamp_min(1e-300))
+                      for a, b in zip(bg, grads)))
     line = {"metric": METRIC, "value": world * 64 * 1e3 / ms_graph, "unit": "instance loss+grad evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -425,6 +428,7 @@ def run_batch(args):
             "one_by_one": {"ms_per_step": ms_eager, "evals_per_s": 64e3 / ms_eager, "launches_per_step": None},
             "graph_vs_one_by_one": ms_eager / ms_graph, "graph_streams": n_streams,
             "tuning_ms": dict(zip(("1", "2", "4", "8"), tuned)), "bitwise_equal_to_one_by_one": bool(same),
+            "max_rel_diff_vs_one_by_one": max_rel,
             "clocks": cl}
     if rank == 0:
         print(json.dumps(line), flush=True)

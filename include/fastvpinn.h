@@ -312,7 +312,11 @@ int fv_graph_destroy(fv_graph graph);
  * fv_batch_loss_grad enqueues the batch as one graph launch on the context's
  * stream; parameters are read from the instances' device buffers at replay
  * time, so they may change between launches (the buffers may not move).
- * Device eps (opts->eps_dev) is not supported in batches.
+ * Device eps (opts->eps_dev) is not supported in batches.  With more than
+ * one stream each instance's tensor-core network kernels run at most one CTA
+ * per SM (room for the other streams' kernels), so their gradient partials
+ * cover other point tiles than in a single call and the FP16/BF16 results
+ * agree with single calls to rounding; all other results are bitwise equal.
  * fv_batch_info: streams in use and the tuning replay times (ms) for
  * 1, 2, 4, 8 streams (0 where not measured). */
 typedef struct fv_batch_s* fv_batch;

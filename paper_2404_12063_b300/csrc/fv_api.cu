@@ -15,6 +15,7 @@ namespace {
 std::mutex g_attr_mu;
 std::map<std::pair<int, const void*>, size_t> g_smem_set;
 std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_res;
 }  // namespace
 
 cudaError_t ensure_smem_attr(fv_ctx ctx, const void* kernel, size_t bytes) {
@@ -40,6 +41,31 @@ int occupancy(fv_ctx ctx, const void* kernel, int threads, size_t smem) {
   }
   std::lock_guard<std::mutex> lk(g_attr_mu);
   g_occ[{ctx->device, kernel, threads, smem}] = n;
+  return n;
+}
+
+int resident_ctas(fv_ctx ctx, const void* kernel, int threads, size_t smem) {
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_res.find({ctx->device, kernel, threads, smem});
+    if (it != g_res.end()) return it->second;
+  }
+  cudaFuncAttributes fa;
+  int regs_sm = 0, thr_sm = 0, smem_sm = 0, reserved = 0;
+  if (ensure_smem_attr(ctx, kernel, smem) != cudaSuccess || cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;     // allocated per warp in units of 256
+  int n = std::min(thr_sm / (warps * 32), regs_sm / std::max(1, regs_warp * warps));
+  n = std::min<int>(n, (int)(smem_sm / (smem + fa.sharedSizeBytes + reserved)));
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  g_res[{ctx->device, kernel, threads, smem}] = n;
   return n;
 }
 
@@ -853,6 +879,7 @@ int batch_capture(fv_batch b, int S) {
     lane_ctx.device = ctx->device;
     lane_ctx.stream = b->streams[lane_of[i]];
     lane_ctx.n_sm = ctx->n_sm;
+    lane_ctx.tc_ctas_cap = S > 1 ? 1 : ctx->tc_ctas_cap;   // leave SM room for the other streams' kernels
     lane_ctx.smem_optin = ctx->smem_optin;
     lane_ctx.smem_per_sm = ctx->smem_per_sm;
     lane_ctx.err_dev = ctx->err_dev;

@@ -70,6 +70,7 @@ struct fv_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   int n_sm = 148;
+  int tc_ctas_cap = 0;              // > 0: at most this many tensor-core MLP CTAs per SM (kernels sharing the GPU)
   size_t smem_optin = 227 * 1024;
   size_t smem_per_sm = 228 * 1024;
   fv::Workspace ws;
@@ -202,6 +203,11 @@ struct KahanR {
 cudaError_t ensure_smem_attr(fv_ctx ctx, const void* kernel, size_t bytes);
 // Resident CTAs per SM for (kernel, threads, dynamic shared memory); 0 on error.
 int occupancy(fv_ctx ctx, const void* kernel, int threads, size_t smem);
+// Resident CTAs per SM from the kernel's registers, shared memory and threads
+// alone.  For the kernels that allocate tensor memory the occupancy query
+// answers one whatever their resources; their callers cap this count by the
+// tensor-memory columns each CTA allocates.
+int resident_ctas(fv_ctx ctx, const void* kernel, int threads, size_t smem);
 
 // ------------------------------------------------------------------ launchers
 // Each returns FV_OK or an error code and enqueues on ctx->stream.

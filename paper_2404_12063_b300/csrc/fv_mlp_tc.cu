@@ -737,12 +737,12 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
   return true;
 }
 
-// Resident CTAs per SM: the hardware occupancy (registers, shared memory)
-// capped so that their tensor-memory allocations fit in 512 columns.
+// Resident CTAs per SM: registers, shared memory and threads, capped so that
+// their tensor-memory allocations fit in 512 columns.
 template <int HP, class OP>
 int tc_ctas_per_sm(fv_ctx ctx, const TcPlan& p, bool reverse) {
-  const int n = reverse ? occupancy(ctx, (const void*)mlp_bwd_tc<HP, OP>, tc_threads<HP>(), p.smem)
-                        : occupancy(ctx, (const void*)mlp_fwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
+  const int n = reverse ? resident_ctas(ctx, (const void*)mlp_bwd_tc<HP, OP>, tc_threads<HP>(), p.smem)
+                        : resident_ctas(ctx, (const void*)mlp_fwd_tc<HP, OP>, tc_threads<HP>(), p.smem);
   return std::max(1, std::min(std::max(n, 1), 512 / p.tmem_cols));
 }
 
@@ -750,7 +750,8 @@ int tc_grid(fv_ctx ctx, const TcPlan& p, bool reverse, bool fp16, int64_t P_tot)
   const int64_t n_tiles = (P_tot + kTile - 1) / kTile;
   const int per = p.HP == 32 ? (fp16 ? tc_ctas_per_sm<32, OpF16>(ctx, p, reverse) : tc_ctas_per_sm<32, OpBF16>(ctx, p, reverse))
                              : (fp16 ? tc_ctas_per_sm<64, OpF16>(ctx, p, reverse) : tc_ctas_per_sm<64, OpBF16>(ctx, p, reverse));
-  return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)ctx->n_sm * per));
+  const int cap = ctx->tc_ctas_cap > 0 ? std::min(per, ctx->tc_ctas_cap) : per;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t)ctx->n_sm * cap));
 }
 
 template <int HP, class OP>

@@ -527,6 +527,25 @@ def test_batch_equals_individual_calls(api, ctx, n_streams):
     assert torch.equal(outs[1][:4], o2[:4]) and torch.equal(grads[1], g2)
 
 
+@pytest.mark.parametrize("n_streams", [1, 3])
+def test_batch_tensor_core_vs_individual_calls(api, ctx, n_streams):
+    """FP16 tensor-core network: one stream gives bitwise the single calls;
+    several streams cap each instance's network kernels at one CTA per SM, so
+    the gradient partials cover other tiles and agree to FP32 rounding."""
+    probs = fi.config5_batch(6)
+    pbs = [api.problem_from_inputs(ctx, p, "fp16", storage="bf16") for p in probs]
+    params = [torch.tensor(p.params, dtype=pb.dtype, device="cuda") for p, pb in zip(probs, pbs)]
+    batch = api.Batch(ctx, pbs, params, n_streams=n_streams)
+    outs, grads = batch.run()
+    for pb, p, o, g in zip(pbs, params, outs, grads):
+        o2, g2 = pb.loss_grad(p)
+        if n_streams == 1:
+            assert torch.equal(o[:4], o2[:4]) and torch.equal(g, g2)
+        else:
+            assert rel(o[:4].cpu().numpy(), o2[:4].cpu().numpy()) < 1e-5
+            assert rel(g.cpu().double().numpy(), g2.cpu().double().numpy()) < 1e-5
+
+
 def test_kernel_timing_records(api, ctx):
     prob = cfg(1)
     pb = api.problem_from_inputs(ctx, prob, "fp32")
