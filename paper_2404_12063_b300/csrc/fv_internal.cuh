@@ -97,6 +97,7 @@ struct fv_mesh_s {
   int n_v = 0;
   int contract_stages[2] = {0, 0};  // tuned stages per CTA (FP32 / FP64 evaluation); 0 = default
   int g_mode = FV_G_STORED;         // contraction from the stored G or matrix-free
+  float* jreg = nullptr;            // regular mode: per element y_eta, x_xi, |J| (FP32), [n_e][3]
 };
 
 struct fv_forcing_s {
@@ -229,7 +230,7 @@ int launch_contract_mfree(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const Ev
 void mfree_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* warps_per_cta, size_t* smem);
 bool regular_supported(fv_mesh mesh, fv_precision prec);
 int regular_grid(fv_ctx ctx, fv_mesh mesh);
-int check_regular_mesh(fv_mesh mesh);
+int check_regular_mesh(fv_mesh mesh, std::vector<float>* scales);
 int launch_contract_regular(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U,
                             void* UB, double eps, const double* eps_dev, double bx, double by, double rscale,
                             double* partials, int* n_partials_out, double* R_out);

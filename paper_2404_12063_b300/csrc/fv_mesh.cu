@@ -305,7 +305,7 @@ extern "C" int fv_mesh_copy_g(fv_mesh m, double* g_host) {
 extern "C" int fv_mesh_destroy(fv_mesh m) {
   clear_error();
   if (!m) return FV_OK;
-  cudaFree(m->G); cudaFree(m->X); cudaFree(m->tables); cudaFree(m->verts); cudaFree(m->cells);
+  cudaFree(m->G); cudaFree(m->X); cudaFree(m->tables); cudaFree(m->verts); cudaFree(m->cells); cudaFree(m->jreg);
   delete m;
   return FV_OK;
 }
@@ -317,8 +317,11 @@ extern "C" int fv_mesh_set_g_mode(fv_mesh m, int mode) {
                "fv_mesh_set_g_mode: mode %d is not 0, 1 or 2", mode);
   if (mode == FV_G_REGULAR) {
     FV_CUDA_TRY(cudaSetDevice(m->ctx->device));
-    const int rc = check_regular_mesh(m);
+    std::vector<float> scales;
+    const int rc = check_regular_mesh(m, &scales);
     if (rc) return rc;
+    if (!m->jreg) FV_CUDA_TRY(cudaMalloc(&m->jreg, sizeof(float) * 3 * (size_t)m->n_e));
+    FV_CUDA_TRY(cudaMemcpy(m->jreg, scales.data(), sizeof(float) * scales.size(), cudaMemcpyHostToDevice));
   }
   m->g_mode = mode;
   return FV_OK;

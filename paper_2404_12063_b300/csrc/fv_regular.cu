@@ -35,20 +35,19 @@ namespace {
 using namespace fv::tc;
 
 constexpr int kRegTile = 128;         // elements per tile (the GEMMs' N)
-constexpr int kRegThreads = 128;      // four warps: one per TMEM lane quarter
+constexpr int kRegThreads = 256;      // eight warps: two per TMEM lane quarter, each on half of the tile's elements
 
 struct RegPlan {
   int Nq_pad;        // K-block width per component: Nq rounded up to 16
   int M2;            // adjoint GEMMs' M (64 or 128 >= Nq); reads may run into the next block (rows >= Nq unused)
   int Nt_blk, K1, nc;
-  int o_A, o_B1, o_B2, o_J, o_red, o_bar, smem;
+  int o_A, o_B1, o_B2, o_J, o_tab, o_red, o_bar, smem;
   int tmem_cols;
 };
 
 struct RegArgs {
   RegPlan pl;
-  const double* verts;
-  const int* cells;
+  const float* J;         // [n_e][3]: y_eta, x_xi, |J| (rectangles)
   const double* tables;   // xi[Q], w[Q], v[T][Q], dv[T][Q]
   int n_e, Q, T;
   const float* F;         // [n_e][T*T]
@@ -76,6 +75,8 @@ bool make_reg_plan(int Q, int T, int nc, RegPlan* p) {
   p->o_B1 = o; o += kRegTile * p->K1 * 2;          // B1 follows A: the adjoint reads past A's last block land here
   p->o_B2 = o; o += kRegTile * p->Nt_blk * 2;
   p->o_J = o; o += kRegTile * 3 * 4;                 // per element J_x, J_y, J
+  p->o_tab = o; o += (Q + 2 * T * Q) * 4;            // FP32 w[Q], v[T][Q], dv[T][Q] (prologue)
+  o = (o + 15) & ~15;
   p->o_red = o; o += 64 * 8;                         // max |Rbar| bits, loss partials
   p->o_bar = o; o += 16;                             // mbarrier + TMEM base
   // D2_0 reuses D1's columns: 256 tensor-memory columns for two components (two CTAs per SM), 512 for
@@ -97,7 +98,7 @@ __device__ __forceinline__ uint16_t to16(float v) {
 }
 
 template <class OP, int NC>
-__global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a) {
+__global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const RegPlan& pl = a.pl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -115,22 +116,23 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // reference matrix [Vxi | Veta (| V)]: rows j = (m, n), columns c Nq_pad + q, q = (a, b)
+  // reference matrix [Vxi | Veta (| V)]: rows j = (m, n), columns c Nq_pad + q, q = (a, b);
+  // products of the one-dimensional tables in FP32 (the entries are rounded to 16 bits)
   {
-    const double* xi = a.tables;
-    const double* w = xi + Q;
-    const double* v = w + Q;
-    const double* dv = v + T * Q;
+    float* tw = reinterpret_cast<float*>(sm + pl.o_tab);
+    float* tv = tw + Q;
+    float* tdv = tv + T * Q;
+    for (int i = tid; i < Q + 2 * T * Q; i += kRegThreads) tw[i] = (float)a.tables[Q + i];
+    __syncthreads();
     for (int idx = tid; idx < Ntb * K1; idx += kRegThreads) {
       const int j = idx / K1, k = idx - j * K1;
       const int c = k / Nqb, q = k - c * Nqb;
       float val = 0.f;
       if (j < Nt && q < Nq) {
         const int m = j / T, n = j - m * T, ia = q / Q, ib = q - ia * Q;
-        const double wq = w[ia] * w[ib];
-        const double r = c == 0 ? dv[m * Q + ia] * v[n * Q + ib]
-                       : c == 1 ? v[m * Q + ia] * dv[n * Q + ib] : v[m * Q + ia] * v[n * Q + ib];
-        val = (float)(wq * r);
+        const float r = c == 0 ? tdv[m * Q + ia] * tv[n * Q + ib]
+                      : c == 1 ? tv[m * Q + ia] * tdv[n * Q + ib] : tv[m * Q + ia] * tv[n * Q + ib];
+        val = (tw[ia] * tw[ib]) * r;
       }
       *reinterpret_cast<uint16_t*>(sA + cm_off(j, k, K1)) = to16<OP>(val);
     }
@@ -146,14 +148,17 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
   uint32_t phase = 0;
   bool failed = false;
   double lsum = 0.0, dsum = 0.0;
-  // TMEM lane of a GEMM row for this thread: M = 128 -> lane = row; M = 64 -> row 16 w + l (l < 16)
-  const int row1 = Ntb == 128 ? tid : (lane < 16 ? warp * 16 + lane : -1);
-  const int row2 = M2 == 128 ? tid : (lane < 16 ? warp * 16 + lane : -1);
-  const uint32_t tRow = (uint32_t)(warp * 32) << 16;
+  // TMEM lane quarter q4 of this warp and its half of the tile's elements (columns);
+  // GEMM row of this thread: M = 128 -> row = lane 32 q4 + l; M = 64 -> row 16 q4 + l (l < 16)
+  const int q4 = warp & 3, c_lo = (warp >> 2) * (kRegTile / 2), c_hi = c_lo + kRegTile / 2;
+  const int row1 = Ntb == 128 ? q4 * 32 + lane : (lane < 16 ? q4 * 16 + lane : -1);
+  const int row2 = M2 == 128 ? q4 * 32 + lane : (lane < 16 ? q4 * 16 + lane : -1);
+  const uint32_t tRow = (uint32_t)(q4 * 32) << 16;
   const int n_tiles = (a.n_e + kRegTile - 1) / kRegTile;
 
   for (int tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     const int e0 = tile * kRegTile;
+    float lt = 0.f, dt = 0.f;            // this tile's loss and eps-derivative terms (FP32; FP64 across tiles)
     // ---- stage the scaled gradient field (B1) and the element scales; each warp takes
     //      four elements at a time and issues all their loads before converting
     for (int n0 = warp * 4; n0 < kRegTile; n0 += kRegThreads / 8) {
@@ -173,13 +178,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int n = n0 + t, e = e0 + n;
-        float jx = 0.f, jy = 0.f, jj = 0.f;
-        if (e < a.n_e) {
-          const Bilin cb = bilin_coeffs(a.verts, a.cells + 4 * (size_t)e);
-          jx = (float)cb.y2;      // y_eta: |J| / (dx/dxi) on a rectangle
-          jy = (float)cb.x1;      // x_xi
-          jj = (float)(cb.x1 * cb.y2);
-        }
+        float jx = 0.f, jy = 0.f, jj = 0.f;    // y_eta = |J| / x_xi, x_xi, |J| on a rectangle
+        if (e < a.n_e) { jx = a.J[3 * (size_t)e]; jy = a.J[3 * (size_t)e + 1]; jj = a.J[3 * (size_t)e + 2]; }
         if (lane == 0) { sJ[n * 3] = jx; sJ[n * 3 + 1] = jy; sJ[n * 3 + 2] = jj; }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -215,21 +215,21 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
     // ---- epilogue 1: R = D1 - F^T, loss, max |Rbar| over the tile (pass A); 32 elements at a time,
     //      their F entries loaded together
     float rmax = 0.f;
-    for (int c = 0; c < kRegTile; c += 32) {
-      float d[32], fv[32];
+    for (int c = c_lo; c < c_hi; c += 16) {
+      float d[16], fv[16];
       const bool rv = row1 >= 0 && row1 < Nt;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) fv[i] = rv && e0 + c + i < a.n_e ? a.F[(size_t)(e0 + c + i) * Nt + row1] : 0.f;
+      for (int i = 0; i < 16; ++i) fv[i] = rv && e0 + c + i < a.n_e ? a.F[(size_t)(e0 + c + i) * Nt + row1] : 0.f;
 #pragma unroll
-      for (int i = 0; i < 32; i += 8) tmem_ld8(tD1 + tRow + c + i, d + i);
+      for (int i = 0; i < 16; i += 8) tmem_ld8(tD1 + tRow + c + i, d + i);
       tmem_wait_ld();
       if (rv) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 16; ++i) {
           const int e = e0 + c + i;
           if (e < a.n_e) {
             const float R = d[i] - fv[i];
-            lsum += (double)R * (double)R;
+            lt = fmaf(R, R, lt);
             rmax = fmaxf(rmax, fabsf(rscale * R));
             if (a.R_out) a.R_out[(size_t)e * Nt + row1] = (double)R;
           }
@@ -250,17 +250,17 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
       }
     }
     // pass B: Rbar s into B2 (rows = elements, K = tests); invalid rows and columns are zero
-    for (int c = 0; c < kRegTile; c += 32) {
-      float d[32], fv[32];
+    for (int c = c_lo; c < c_hi; c += 16) {
+      float d[16], fv[16];
       const bool rv = row1 >= 0 && row1 < Nt;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) fv[i] = rv && e0 + c + i < a.n_e ? a.F[(size_t)(e0 + c + i) * Nt + row1] : 0.f;
+      for (int i = 0; i < 16; ++i) fv[i] = rv && e0 + c + i < a.n_e ? a.F[(size_t)(e0 + c + i) * Nt + row1] : 0.f;
 #pragma unroll
-      for (int i = 0; i < 32; i += 8) tmem_ld8(tD1 + tRow + c + i, d + i);
+      for (int i = 0; i < 16; i += 8) tmem_ld8(tD1 + tRow + c + i, d + i);
       tmem_wait_ld();
       if (row1 >= 0) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 16; ++i) {
           const int e = e0 + c + i;
           const float rb = rv && e < a.n_e ? sc * rscale * (d[i] - fv[i]) : 0.f;
           *reinterpret_cast<uint16_t*>(sB2 + cm_off(c + i, row1, Ntb)) = to16<OP>(rb);
@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
       }
     }
     if (!a.UB) {
+      lsum += (double)lt;
       tc_fence_before();
       __syncthreads();
       continue;
@@ -291,40 +292,39 @@ __global__ void __launch_bounds__(kRegThreads, 1) contract_regular_tc(RegArgs a)
     phase ^= 1;
     if (__syncthreads_or(!ok)) { failed = true; if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); break; }
     tc_fence_after();
-    // ---- epilogue 2: seeds and the eps derivative, 16 elements at a time
+    // ---- epilogue 2: seeds and the eps derivative, 8 elements at a time
     const float inv = 1.f / sc;
     const bool qv = row2 >= 0 && row2 < Nq;
-    for (int c = 0; c < kRegTile; c += 16) {
-      float dx[16], dy[16], dvv[16], ux[16], uy[16];
+    for (int c = c_lo; c < c_hi; c += 8) {
+      float dx[8], dy[8], dvv[8], ux[8], uy[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < 8; ++i) {
         const bool in = qv && e0 + c + i < a.n_e;
         const int64_t p = (int64_t)(e0 + c + i) * Nq + row2;
         ux[i] = in ? a.U[a.P_tot + p] : 0.f;
         uy[i] = in ? a.U[2 * a.P_tot + p] : 0.f;
       }
-#pragma unroll
-      for (int i = 0; i < 16; i += 8) {
-        tmem_ld8(tD2 + tRow + c + i, dx + i);
-        tmem_ld8(tD2 + kRegTile + tRow + c + i, dy + i);
-        if (NC == 3) tmem_ld8(tD2 + 2 * kRegTile + tRow + c + i, dvv + i);
-      }
+      tmem_ld8(tD2 + tRow + c, dx);
+      tmem_ld8(tD2 + kRegTile + tRow + c, dy);
+      if (NC == 3) tmem_ld8(tD2 + 2 * kRegTile + tRow + c, dvv);
       tmem_wait_ld();
       if (qv) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 8; ++i) {
           const int n = c + i, e = e0 + n;
           if (e >= a.n_e) continue;
           const float jx = sJ[n * 3], jy = sJ[n * 3 + 1], jj = sJ[n * 3 + 2];
           const float sx = dx[i] * inv, sy = dy[i] * inv, sv = NC == 3 ? dvv[i] * inv : 0.f;
           const int64_t p = (int64_t)e * Nq + row2;
-          dsum += (double)(jx * ux[i] * sx + jy * uy[i] * sy);
+          dt += jx * ux[i] * sx + jy * uy[i] * sy;
           a.UB[p] = 0.f;
           a.UB[a.P_tot + p] = eps * jx * sx + bx * jj * sv;
           a.UB[2 * a.P_tot + p] = eps * jy * sy + by * jj * sv;
         }
       }
     }
+    lsum += (double)lt;
+    dsum += (double)dt;
     tc_fence_before();
     __syncthreads();
   }
@@ -369,7 +369,8 @@ int regular_grid(fv_ctx ctx, fv_mesh m) {
 }
 
 // Every element an axis-aligned rectangle: x depends on xi only, y on eta only.
-int check_regular_mesh(fv_mesh m) {
+// Fills `scales` with each element's y_eta, x_xi and |J| = x_xi y_eta in FP32.
+int check_regular_mesh(fv_mesh m, std::vector<float>* scales) {
   std::vector<double> v(2 * (size_t)m->n_v);
   std::vector<int> c(4 * (size_t)m->n_e);
   cudaError_t e = cudaMemcpy(v.data(), m->verts, v.size() * sizeof(double), cudaMemcpyDeviceToHost);
@@ -391,6 +392,11 @@ int check_regular_mesh(fv_mesh m) {
                 "diagonal Jacobian)", k);
       return FV_ERR_ARG;
     }
+    if (scales) {
+      scales->push_back((float)y2);
+      scales->push_back((float)x1);
+      scales->push_back((float)(x1 * y2));
+    }
   }
   return FV_OK;
 }
@@ -403,7 +409,11 @@ int launch_contract_regular(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan&
     set_error("regular-mesh contraction: Q = %d, T = %d outside Q*Q, T*T <= 128", m->Q, m->T);
     return FV_ERR_UNSUPPORTED;
   }
-  a.verts = m->verts; a.cells = m->cells; a.tables = m->tables;
+  if (!m->jreg) {
+    set_error("regular-mesh contraction: the mesh has no element scales (set FV_G_REGULAR first)");
+    return FV_ERR_ARG;
+  }
+  a.J = m->jreg; a.tables = m->tables;
   a.n_e = m->n_e; a.Q = m->Q; a.T = m->T;
   a.F = f->F32;
   a.U = static_cast<const float*>(U); a.UB = static_cast<float*>(UB); a.P_tot = pl.P_tot;
