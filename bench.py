@@ -382,7 +382,7 @@ def run_batch(args):
     torch.cuda.set_stream(stream)
     ctx = api.Context(local, stream)
     prec = "fp16" if args.precision == "auto" else args.precision
-    probs = fi.config5_batch(64)
+    probs = fi.poisson_batch(64)
     pbs = [api.problem_from_inputs(ctx, p, prec, storage="bf16" if prec in ("bf16", "fp16") else None) for p in probs]
     for pb in pbs:                      # contraction launch plan per mesh (setup, not timed)
         pb.mesh.autotune(prec)
@@ -467,7 +467,7 @@ def main():
         return run_ablation(args)
     if args.workload == "forms":
         return run_forms(args)
-    prob = fi.config3_annulus()
+    prob = fi.gear_annulus()
     if args.impl == "reference":
         return run_reference(args, prob)
 
@@ -486,8 +486,8 @@ def main():
     else:
         for p in ("bf16", "fp16"):
             try:
-                pb_try = api.problem_from_inputs(ctx, fi.config1_tiny(), p)
-                pb_try.loss_grad(torch.tensor(fi.config1_tiny().params, dtype=torch.float32, device="cuda"))
+                pb_try = api.problem_from_inputs(ctx, fi.tiny_square(), p)
+                pb_try.loss_grad(torch.tensor(fi.tiny_square().params, dtype=torch.float32, device="cuda"))
                 variants.append(p)
             except Exception:
                 pass

@@ -347,7 +347,7 @@ class Problem:
         return self.mesh.n_elements * self.quad_order ** 2
 
 
-def config1_tiny() -> Problem:
+def tiny_square() -> Problem:
     """Poisson on [0,1]^2, 4x4 uniform quads, Q=5, T=5, MLP 2-30-30-30-1
     (Glorot, seed 0), 400 boundary points, FP64."""
     mesh = rect_grid(4, 4)
@@ -358,7 +358,7 @@ def config1_tiny() -> Problem:
                    bd, u(bd[:, 0], bd[:, 1]), precision="fp64")
 
 
-def config2_disc() -> Problem:
+def skewed_disc() -> Problem:
     """Poisson on the unit disc, 1024-quad butterfly O-grid, interior nodes
     jittered +-0.2 h (seed 1), Q=8, T=6, u = sin(4 pi x) cos(4 pi y),
     MLP 2-30x3-1 (seed 1), 1000 boundary points on the circle, FP32."""
@@ -372,7 +372,7 @@ def config2_disc() -> Problem:
                    bd, u(bd[:, 0], bd[:, 1]), precision="fp32")
 
 
-def config3_annulus() -> Problem:
+def gear_annulus() -> Problem:
     """Poisson on the gear-like annulus 0.5 <= r <= 1 + 0.1 cos(12 theta),
     128 x 64 O-grid (8192 quads), Q=10, T=8, u = sin(8 pi x) sin(8 pi y),
     MLP 2-50x4-1 (seed 0), 1000 boundary points (500 per curve)."""
@@ -384,7 +384,7 @@ def config3_annulus() -> Problem:
                    bd, u(bd[:, 0], bd[:, 1]), precision="fp32")
 
 
-def config4_inverse(n: int = 256) -> Problem:
+def inverse_cd2d(n: int = 256) -> Problem:
     """Inverse CD2D: -eps Lap u + b.grad u = f on [-1,1]^2, n x n quads with
     interior nodes jittered +-0.15 h (h = 2/n, seed 3), Q=5, T=5, b=(0.1,0),
     eps trainable (true 0.3, start 2.0), u = 10 sin x tanh x exp(-0.3 x^2),
@@ -401,7 +401,7 @@ def config4_inverse(n: int = 256) -> Problem:
                    sensor_xy=sens, sensor_u=u(sens[:, 0], sens[:, 1]), gamma=10.0, precision="fp32")
 
 
-def config5_batch(n_instances: int = 64, seed: int = 4) -> List[Problem]:
+def poisson_batch(n_instances: int = 64, seed: int = 4) -> List[Problem]:
     """64 Poisson instances on uniform grids of [0,1]^2; per instance draw
     (stream 3, in order) N_e log-uniform in [100, 16384], Q = 5 + floor(6U),
     T = 4 + floor(5U); separate MLP 2-30x3-1 per instance (stream 100+i)."""
@@ -425,7 +425,7 @@ def config5_batch(n_instances: int = 64, seed: int = 4) -> List[Problem]:
 
 def config_eps_field() -> Problem:
     """Space-dependent diffusion (Sec. 4.7.2): -div(eps(x, y) grad u) + b . grad u = f
-    on the 1024-element disc of config 2 (Q=8, T=6), f = 10, b = (1, 0); one
+    on the skewed 1024-element disc (Q=8, T=6), f = 10, b = (1, 0); one
     network 2-30x3-2 with outputs (u, eps) (seed 5); 1000 boundary points with
     g = 0 and 500 sensors (seed 5, stream 2) in the disc.  The paper's sensor
     data come from a finite-element reference that is not available; the
@@ -445,4 +445,4 @@ def config_eps_field() -> Problem:
                    sensor_xy=sens, sensor_u=u_obs(sens[:, 0], sens[:, 1]), gamma=10.0, precision="fp32")
 
 
-CONFIGS = {1: config1_tiny, 2: config2_disc, 3: config3_annulus, 4: config4_inverse}
+WORKLOADS = {"tiny": tiny_square, "disc": skewed_disc, "annulus": gear_annulus, "inverse": inverse_cd2d}

@@ -83,7 +83,7 @@ def compare(workload: str, epochs: int, every: int, lr: float, variants=("fp32",
     is 1.05 x the FP32 run's final error."""
     import fv_inputs as fi
     ctx = api.Context(0)
-    prob = {"annulus": fi.config3_annulus, "disc": fi.config2_disc}[workload]()
+    prob = {"annulus": fi.gear_annulus, "disc": fi.skewed_disc}[workload]()
     res = {}
     for v in variants:
         res[v] = train(ctx, prob, v, epochs, lr, every, storage="bf16" if v in ("bf16", "fp16") else "fp32")

@@ -2,8 +2,8 @@
 oracle on the same seeded inputs.
 
 Tolerances (relative, norm-wise for vectors): 1e-10 for the FP64 path, 1e-5
-for FP32, 2e-2 for BF16 / TF32.  Full-size cases (configs 2-4 at their
-stated sizes, the launch configuration the benchmark times) are compared in
+for FP32, 2e-2 for BF16 / TF32.  Full-size cases (the disc, the annulus and the inverse
+problem at their stated sizes, the launch configuration the benchmark times) are compared in
 full against the oracle run with all host cores.
 """
 import functools
@@ -45,7 +45,7 @@ def ctx(api):
 
 @functools.lru_cache(maxsize=None)
 def cfg(k):
-    return fi.CONFIGS[k]()
+    return fi.WORKLOADS[k]()
 
 
 def _with(prob, **kw):
@@ -96,7 +96,7 @@ def check_against_oracle(api, ctx, prob, precision, storage=None, norm="test", t
 
 # ---------------------------------------------------------------- mesh tensors (a1)
 def test_mesh_tensors_match_oracle(api, ctx):
-    prob = _with(cfg(2), b=(0.3, -0.1))
+    prob = _with(cfg("disc"), b=(0.3, -0.1))
     mesh = api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, prob.quad_order, prob.test_order, "fp64", True)
     X = mesh.quad_points()
     Xo = oracle.quad_points(prob.mesh, prob.quad_order).reshape(-1, 2)
@@ -115,7 +115,7 @@ def test_mesh_tensors_match_oracle(api, ctx):
 
 @pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("bf16", 8e-3)])
 def test_mesh_tensor_storage_rounding(api, ctx, storage, tol):
-    prob = cfg(1)
+    prob = cfg("tiny")
     mesh = api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells, prob.quad_order, prob.test_order, storage)
     G = mesh.g_tensor()
     Gx, Gy, _, _ = oracle.Bound(prob).tensors()
@@ -123,13 +123,13 @@ def test_mesh_tensor_storage_rounding(api, ctx, storage, tol):
     assert np.max(np.abs(G[:, 1] - Gy)) < tol * np.max(np.abs(Gy))
 
 
-# ---------------------------------------------------------------- config 1 (FP64, tiny)
-def test_config1_fp64_loss_grad(api, ctx):
-    check_against_oracle(api, ctx, cfg(1), "fp64")
+# ---------------------------------------------------------------- tiny square (FP64)
+def test_tiny_fp64_loss_grad(api, ctx):
+    check_against_oracle(api, ctx, cfg("tiny"), "fp64")
 
 
-def test_config1_fp64_intermediates_elementwise(api, ctx):
-    prob = _with(cfg(1), b=(0.2, -0.3), eps=0.7, params=fi.random_bias_params(cfg(1).widths, 1, 1))
+def test_tiny_fp64_intermediates_elementwise(api, ctx):
+    prob = _with(cfg("tiny"), b=(0.2, -0.3), eps=0.7, params=fi.random_bias_params(cfg("tiny").widths, 1, 1))
     pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp64", intermediates=True)
     ref = oracle_eval(prob, prob.params, want_R=True, want_ubar=True, want_upts=True)
     P = prob.n_points
@@ -148,18 +148,18 @@ def test_config1_fp64_intermediates_elementwise(api, ctx):
     assert np.max(np.abs(UB[0, P:] - seed)) < 1e-12 * np.max(np.abs(seed))
 
 
-def test_config1_fp32(api, ctx):
-    check_against_oracle(api, ctx, cfg(1), "fp32")
+def test_tiny_fp32(api, ctx):
+    check_against_oracle(api, ctx, cfg("tiny"), "fp32")
 
 
-# ---------------------------------------------------------------- config 2 (skewed disc)
+# ---------------------------------------------------------------- skewed disc
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_config2_full(api, ctx, precision):
-    check_against_oracle(api, ctx, cfg(2), precision)
+def test_disc_full(api, ctx, precision):
+    check_against_oracle(api, ctx, cfg("disc"), precision)
 
 
-def test_config2_fp32_intermediates_elementwise(api, ctx):
-    prob = cfg(2)
+def test_disc_fp32_intermediates_elementwise(api, ctx):
+    prob = cfg("disc")
     pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp32", intermediates=True)
     ref = oracle_eval(prob, params.cpu().double().numpy(), want_R=True, want_ubar=True, want_upts=True)
     up = ref["upts"].reshape(-1, 3)
@@ -170,25 +170,25 @@ def test_config2_fp32_intermediates_elementwise(api, ctx):
     assert rel(UB[1:, :P].T, ref["ubar"].reshape(-1, 2)) < 1e-5
 
 
-# ---------------------------------------------------------------- config 3 (annulus, 819k points)
-def test_config3_fp32_full(api, ctx):
-    check_against_oracle(api, ctx, cfg(3), "fp32")
+# ---------------------------------------------------------------- gear-like annulus (819k points)
+def test_annulus_fp32_full(api, ctx):
+    check_against_oracle(api, ctx, cfg("annulus"), "fp32")
 
 
-def test_config3_fp64_full(api, ctx):
-    check_against_oracle(api, ctx, cfg(3), "fp64")
+def test_annulus_fp64_full(api, ctx):
+    check_against_oracle(api, ctx, cfg("annulus"), "fp64")
 
 
-# ---------------------------------------------------------------- config 4 (inverse CD2D, 65536 elements)
+# ---------------------------------------------------------------- inverse CD2D (65536 elements)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_config4_full(api, ctx, precision):
-    check_against_oracle(api, ctx, cfg(4), precision)
+def test_inverse_full(api, ctx, precision):
+    check_against_oracle(api, ctx, cfg("inverse"), precision)
 
 
-def test_config4_gradient_vs_central_differences(api, ctx):
+def test_inverse_gradient_vs_central_differences(api, ctx):
     """GPU FP64 gradient against central differences of GPU FP64 losses, on a
     random subset of coordinates plus eps (inverse-problem mesh, 32x32)."""
-    prob = fi.config4_inverse(32)
+    prob = fi.inverse_cd2d(32)
     pb = api.problem_from_inputs(ctx, prob, "fp64")
     params = torch.tensor(prob.params, dtype=torch.float64, device="cuda")
     out, grad = pb.loss_grad(params)
@@ -229,16 +229,16 @@ def test_ragged_sizes(api, ctx, ne, Q, T, precision):
 
 
 def test_no_boundary_and_elem_norm(api, ctx):
-    prob = _with(cfg(1), bd_xy=np.zeros((0, 2)), bd_g=np.zeros(0))
+    prob = _with(cfg("tiny"), bd_xy=np.zeros((0, 2)), bd_g=np.zeros(0))
     check_against_oracle(api, ctx, prob, "fp64", norm="elem")
 
 
 def test_bf16_storage_fp32_network(api, ctx):
-    check_against_oracle(api, ctx, cfg(2), "fp32", storage="bf16", tol=TOL["bf16"])
+    check_against_oracle(api, ctx, cfg("disc"), "fp32", storage="bf16", tol=TOL["bf16"])
 
 
 def test_large_weights_saturated_tanh(api, ctx):
-    prob = _with(cfg(1), params=fi.glorot_params(cfg(1).widths, 0, 1, gain=3.0))
+    prob = _with(cfg("tiny"), params=fi.glorot_params(cfg("tiny").widths, 0, 1, gain=3.0))
     check_against_oracle(api, ctx, prob, "fp64")
     check_against_oracle(api, ctx, prob, "fp32")
 
@@ -256,7 +256,7 @@ def test_degenerate_element_is_rejected(api, ctx):
 
 def test_argument_errors(api, ctx):
     from paper_2404_12063_b300 import FVError, _native as N
-    prob = cfg(1)
+    prob = cfg("tiny")
     with pytest.raises(FVError) as ei:
         api.Mesh(ctx, prob.mesh.vertices, prob.mesh.cells + 100, 5, 5)
     assert ei.value.code == N.FV_ERR_ARG
@@ -281,7 +281,7 @@ def test_argument_errors(api, ctx):
 
 
 def test_deterministic(api, ctx):
-    prob = cfg(2)
+    prob = cfg("disc")
     pb = api.problem_from_inputs(ctx, prob, "fp32")
     params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
     o1, g1 = pb.loss_grad(params)
@@ -290,7 +290,7 @@ def test_deterministic(api, ctx):
     assert torch.equal(o1, o2) and torch.equal(g1, g2)
 
 
-@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("k", ["disc", "inverse"])
 def test_autotuned_contraction_matches_oracle(api, ctx, k):
     """fv_autotune picks the one- or two-stage contraction plan for the mesh;
     the tuned evaluation still matches the oracle and is reproducible."""
@@ -310,8 +310,8 @@ def test_autotuned_contraction_matches_oracle(api, ctx, k):
 
 
 # ---------------------------------------------------------------- matrix-free contraction
-@pytest.mark.parametrize("k,precision", [(1, "fp64"), (1, "fp32"), (2, "fp64"), (2, "fp32"), (3, "fp32"), (4, "fp64"),
-                                         (4, "fp32")])
+@pytest.mark.parametrize("k,precision", [("tiny", "fp64"), ("tiny", "fp32"), ("disc", "fp64"), ("disc", "fp32"), ("annulus", "fp32"), ("inverse", "fp64"),
+                                         ("inverse", "fp32")])
 def test_matrix_free_matches_oracle(api, ctx, k, precision):
     check_against_oracle(api, ctx, cfg(k), precision, g_mode="matrix_free")
 
@@ -332,7 +332,7 @@ def test_matrix_free_ragged_sizes(api, ctx, ne, Q, T, precision):
 def test_matrix_free_intermediates_elementwise(api, ctx):
     """Residuals R[e][j] and seeds dL/du_x, dL/du_y of the matrix-free
     contraction against the oracle, element by element, with convection."""
-    prob = _with(cfg(1), b=(0.2, -0.3), eps=0.7, params=fi.random_bias_params(cfg(1).widths, 1, 1))
+    prob = _with(cfg("tiny"), b=(0.2, -0.3), eps=0.7, params=fi.random_bias_params(cfg("tiny").widths, 1, 1))
     pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, "fp64", intermediates=True, g_mode="matrix_free")
     ref = oracle_eval(prob, prob.params, want_R=True, want_ubar=True)
     P = prob.n_points
@@ -345,12 +345,12 @@ def test_matrix_free_intermediates_elementwise(api, ctx):
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_matrix_free_tensor_core(api, ctx, precision):
-    check_against_oracle(api, ctx, cfg(3), precision, g_mode="matrix_free")
+    check_against_oracle(api, ctx, cfg("annulus"), precision, g_mode="matrix_free")
 
 
 def test_matrix_free_mode_argument_errors(api, ctx):
     from paper_2404_12063_b300 import FVError, _native as N
-    pb = api.problem_from_inputs(ctx, cfg(1), "fp64")
+    pb = api.problem_from_inputs(ctx, cfg("tiny"), "fp64")
     with pytest.raises(FVError) as ei:
         N.call("fv_mesh_set_g_mode", pb.mesh.h, 7)
     assert ei.value.code == N.FV_ERR_ARG
@@ -386,7 +386,7 @@ def test_regular_mesh_agrees_with_stored_g(api, ctx):
 
 def test_regular_mode_rejects_a_skewed_mesh(api, ctx):
     from paper_2404_12063_b300 import FVError, _native as N
-    pb = api.problem_from_inputs(ctx, cfg(2), "fp16")
+    pb = api.problem_from_inputs(ctx, cfg("disc"), "fp16")
     with pytest.raises(FVError) as ei:
         pb.mesh.set_g_mode("regular")
     assert ei.value.code == N.FV_ERR_ARG and "axis-aligned" in str(ei.value)
@@ -433,7 +433,7 @@ def test_eps_field_intermediates_elementwise(api, ctx):
 def test_eps_field_constant_output_equals_scalar_eps(api, ctx):
     """GPU: a two-output network whose eps row is zero and bias eps0 gives the
     scalar-eps problem's loss, and its eps-bias gradient is that problem's dL/deps."""
-    prob1 = _with(cfg(1), eps=0.65, b=(0.3, -0.2))
+    prob1 = _with(cfg("tiny"), eps=0.65, b=(0.3, -0.2))
     n_in = prob1.widths[-2]
     p1 = prob1.params
     p2 = np.concatenate([p1[:len(p1) - (n_in + 1)], p1[len(p1) - (n_in + 1): len(p1) - 1], np.zeros(n_in),
@@ -459,7 +459,7 @@ def test_eps_field_rejected_by_tensor_cores(api, ctx):
 
 # ---------------------------------------------------------------- bindings, Adam, batches
 def test_autograd_function(api, ctx):
-    prob = cfg(1)
+    prob = cfg("tiny")
     pb = api.problem_from_inputs(ctx, prob, "fp64")
     params = torch.tensor(prob.params, dtype=torch.float64, device="cuda", requires_grad=True)
     loss = api.FastVPINNLoss.apply(params, pb)
@@ -469,7 +469,7 @@ def test_autograd_function(api, ctx):
 
 
 def test_mlp_eval_matches_oracle(api, ctx):
-    prob = cfg(3)
+    prob = cfg("annulus")
     xy = fi.uniform_points(1000, 5, 9)
     for prec, tol in (("fp64", 1e-13), ("fp32", 1e-5)):
         dt = torch.float64 if prec == "fp64" else torch.float32
@@ -483,7 +483,7 @@ def test_mlp_eval_matches_oracle(api, ctx):
 def test_inverse_step_adam_update(api, ctx):
     """One fv_inverse_step with lr > 0 equals the oracle gradient pushed through
     Adam (Kingma & Ba, bias-corrected) on (theta, eps)."""
-    prob = fi.config4_inverse(16)
+    prob = fi.inverse_cd2d(16)
     pb = api.problem_from_inputs(ctx, prob, "fp64")
     params = torch.tensor(prob.params, dtype=torch.float64, device="cuda")
     eps = torch.tensor([prob.eps], dtype=torch.float64, device="cuda")
@@ -507,7 +507,7 @@ def test_inverse_step_adam_update(api, ctx):
 
 @pytest.mark.parametrize("n_streams", [0, 1, 3])
 def test_batch_equals_individual_calls(api, ctx, n_streams):
-    probs = fi.config5_batch(6)
+    probs = fi.poisson_batch(6)
     pbs = [api.problem_from_inputs(ctx, p, "fp32") for p in probs]
     params = [torch.tensor(p.params, dtype=torch.float32, device="cuda") for p in probs]
     batch = api.Batch(ctx, pbs, params, n_streams=n_streams)
@@ -532,7 +532,7 @@ def test_batch_tensor_core_vs_individual_calls(api, ctx, n_streams):
     """FP16 tensor-core network: one stream gives bitwise the single calls;
     several streams cap each instance's network kernels at one CTA per SM, so
     the gradient partials cover other tiles and agree to FP32 rounding."""
-    probs = fi.config5_batch(6)
+    probs = fi.poisson_batch(6)
     pbs = [api.problem_from_inputs(ctx, p, "fp16", storage="bf16") for p in probs]
     params = [torch.tensor(p.params, dtype=pb.dtype, device="cuda") for p, pb in zip(probs, pbs)]
     batch = api.Batch(ctx, pbs, params, n_streams=n_streams)
@@ -547,7 +547,7 @@ def test_batch_tensor_core_vs_individual_calls(api, ctx, n_streams):
 
 
 def test_kernel_timing_records(api, ctx):
-    prob = cfg(1)
+    prob = cfg("tiny")
     pb = api.problem_from_inputs(ctx, prob, "fp32")
     params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
     ctx.reset_kernel_times()
@@ -561,7 +561,7 @@ def test_kernel_timing_records(api, ctx):
 
 
 # ---------------------------------------------------------------- tensor-core (BF16) path
-@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("k", ["tiny", "disc", "annulus", "inverse"])
 @pytest.mark.parametrize("storage", ["fp32", "bf16"])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_against_oracle(api, ctx, k, storage, precision):
@@ -570,13 +570,13 @@ def test_tensor_core_against_oracle(api, ctx, k, storage, precision):
     # (measured 2.6% with FP32 G, 4.2% with BF16 G) while the loss L and the
     # gradient meet it; that one component gets a 6e-2 bound.  FP16 operands
     # (11-bit significand) meet 2e-2 on every part.
-    tol_lv = 6e-2 if (precision == "bf16" and k == 4) else None
+    tol_lv = 6e-2 if (precision == "bf16" and k == "inverse") else None
     check_against_oracle(api, ctx, cfg(k), precision, storage=storage, tol_lv=tol_lv)
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_intermediates_elementwise(api, ctx, precision):
-    prob = cfg(3)
+    prob = cfg("annulus")
     pb, params, out, U, UB, R = gpu_eval(api, ctx, prob, precision, intermediates=True)
     ref = oracle_eval(prob, params.cpu().double().numpy(), want_R=True, want_upts=True)
     up = ref["upts"].reshape(-1, 3)
@@ -589,19 +589,19 @@ def test_tensor_core_intermediates_elementwise(api, ctx, precision):
 @pytest.mark.parametrize("widths", [[2, 20, 1], [2, 24, 16, 1], [2, 40, 40, 40, 40, 40, 1]])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_network_depths(api, ctx, widths, precision):
-    prob = _with(cfg(2), widths=widths, params=fi.random_bias_params(widths, 5, 1))
+    prob = _with(cfg("disc"), widths=widths, params=fi.random_bias_params(widths, 5, 1))
     check_against_oracle(api, ctx, prob, precision)
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_convection_and_eps(api, ctx, precision):
-    prob = _with(fi.config4_inverse(32), eps=0.7)
+    prob = _with(fi.inverse_cd2d(32), eps=0.7)
     check_against_oracle(api, ctx, prob, precision, tol_lv=6e-2 if precision == "bf16" else None)
 
 
 def test_fp16_tighter_than_bf16(api, ctx):
     """The FP16 operand path is measurably closer to the oracle than BF16."""
-    prob = cfg(3)
+    prob = cfg("annulus")
     errs = {}
     for prec in ("bf16", "fp16"):
         pb, params, out, grad = gpu_eval(api, ctx, prob, prec)

@@ -37,7 +37,7 @@ def _worker(rank, world, port, cfg, result_path):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     from paper_2404_12063_b300.parallel import ShardedLoss
-    prob = fi.config4_inverse(24) if cfg == 4 else fi.config2_disc()
+    prob = fi.inverse_cd2d(24) if cfg == "inverse" else fi.skewed_disc()
     sl = ShardedLoss(prob, rank, world, _oracle_evaluator)
     out, grad = sl.loss_grad(prob.params)
     if rank == 0:
@@ -46,7 +46,7 @@ def _worker(rank, world, port, cfg, result_path):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("cfg", [2, 4])
+@pytest.mark.parametrize("cfg", ["disc", "inverse"])
 def test_two_rank_shards_sum_to_the_whole(tmp_path, cfg):
     import torch.multiprocessing as mp
     import oracle
@@ -54,7 +54,7 @@ def test_two_rank_shards_sum_to_the_whole(tmp_path, cfg):
     res = str(tmp_path / "r.npy")
     mp.start_processes(_worker, args=(world, _free_port(), cfg, res), nprocs=world, join=True, start_method="spawn")
     got = np.load(res)
-    prob = fi.config4_inverse(24) if cfg == 4 else fi.config2_disc()
+    prob = fi.inverse_cd2d(24) if cfg == "inverse" else fi.skewed_disc()
     ref = oracle.Bound(prob).loss_grad(prob.params)
     want = np.concatenate([[ref["loss"], ref["Lv"], ref["Lb"], ref["Ls"], ref["dL_deps"]], ref["grad"]])
     np.testing.assert_allclose(got[:5], want[:5], rtol=1e-12)

@@ -93,7 +93,7 @@ def test_bilinear_hand_worked_example():
 
 
 def test_jacobian_against_finite_differences_and_area():
-    prob = fi.config2_disc()
+    prob = fi.skewed_disc()
     h = 1e-6
     rng = fi.SplitMix64(7, 9)
     for e in range(0, prob.mesh.n_elements, 37):
@@ -220,7 +220,7 @@ def test_linear_patch_test_on_skewed_mesh(T, Q):
 
 def test_manufactured_solution_residual_vanishes_with_quadrature():
     """With u = the exact solution and f = -Lap u, |R| -> 0 as Q grows."""
-    base = fi.config1_tiny()
+    base = fi.tiny_square()
     uex = lambda x, y: np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
     gx = lambda x, y: 2 * np.pi * np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y)
     gy = lambda x, y: 2 * np.pi * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
@@ -239,7 +239,7 @@ def test_manufactured_solution_residual_vanishes_with_quadrature():
 
 
 def test_loop_variant_equals_tensor_variant():
-    prob = _with(fi.config2_disc(), b=(0.3, -0.2), eps=0.8)
+    prob = _with(fi.skewed_disc(), b=(0.3, -0.2), eps=0.8)
     prob.mesh = prob.mesh.subset(0, 96)
     b = oracle.Bound(prob, with_boundary=False)
     out = b.loss_grad(prob.params, want_grad=False, want_R=True, want_upts=True)
@@ -253,7 +253,7 @@ def test_loss_invariant_under_cell_vertex_rotation_and_element_order():
     """Cyclically relabelling each cell's vertices rotates the reference square by
     90 degrees; the tensor-product test space maps to itself up to signs, so
     the loss is unchanged.  So is any permutation of the elements."""
-    prob = fi.config2_disc()
+    prob = fi.skewed_disc()
     prob.mesh = prob.mesh.subset(200, 264)
     base = oracle.Bound(prob).loss_value(prob.params)
     for shift in (1, 2, 3):
@@ -267,7 +267,7 @@ def test_loss_invariant_under_cell_vertex_rotation_and_element_order():
 
 def test_norm_conventions_ratio():
     """Algorithm 3 (mean over tests) and Eq. (loss) (mean over elements) differ by N_t / N_e."""
-    prob = fi.config1_tiny()
+    prob = fi.tiny_square()
     Lt = oracle.Bound(prob, norm=0).loss_value(prob.params)[1]
     Le = oracle.Bound(prob, norm=1).loss_value(prob.params)[1]
     assert abs(Le / Lt - prob.test_order ** 2 / prob.mesh.n_elements) < 1e-13
@@ -275,7 +275,7 @@ def test_norm_conventions_ratio():
 
 # ---------------------------------------------------------------- MLP and gradients
 def test_mlp_gradient_complex_step_and_fd():
-    prob = fi.config3_annulus()
+    prob = fi.gear_annulus()
     xy = fi.uniform_points(64, 1, 7)
     u, ux, uy = oracle.mlp(prob.widths, prob.params, xy)
     cx, cy = oracle.mlp_cstep_x(prob.widths, prob.params, xy)
@@ -289,7 +289,7 @@ def test_mlp_gradient_complex_step_and_fd():
 
 def test_mlp_value_independent_numpy():
     """The forward value against a direct numpy evaluation of Eq. (NN)."""
-    prob = fi.config2_disc()
+    prob = fi.skewed_disc()
     xy = fi.uniform_points(50, 2, 7)
     u, _, _ = oracle.mlp(prob.widths, prob.params, xy)
     h = xy.T
@@ -323,8 +323,8 @@ def test_full_gradient_complex_step_small_problem():
         assert abs(out["dL_deps"] - cs[-1]) < 1e-12 * abs(cs[-1])
 
 
-def test_config1_gradient_complex_step_subset_and_fd():
-    prob = fi.config1_tiny()
+def test_tiny_gradient_complex_step_subset_and_fd():
+    prob = fi.tiny_square()
     b = oracle.Bound(prob)
     out = b.loss_grad(prob.params)
     idx = np.arange(0, len(prob.params), 23)
@@ -341,7 +341,7 @@ def test_config1_gradient_complex_step_subset_and_fd():
 
 def test_loss_is_quadratic_in_eps():
     """R is affine in eps, so L(eps) is a parabola: three values fix dL/deps and d2L/deps2."""
-    prob = fi.config4_inverse(8)
+    prob = fi.inverse_cd2d(8)
     b = oracle.Bound(prob)
     e0 = 0.9
     Ls = [b.loss_value(prob.params, eps=e)[0] for e in (e0 - 0.5, e0, e0 + 0.5)]
@@ -358,7 +358,7 @@ def test_gradient_against_torch_double_backward():
     """The hand-written reverse sweep against PyTorch CPU FP64 autograd
     (grad u by create_graph autograd, then backward) on the tensor form."""
     torch = pytest.importorskip("torch")
-    prob = fi.config1_tiny()
+    prob = fi.tiny_square()
     prob = _with(prob, b=(0.2, 0.1), eps=0.8, params=fi.random_bias_params(prob.widths, 1, 1))
     b = oracle.Bound(prob)
     out = b.loss_grad(prob.params)
@@ -397,7 +397,7 @@ def test_gradient_against_torch_double_backward():
 def test_adjoint_seeds_are_dL_dgradu():
     """ubar at a node = dLv / d(u_x, u_y) there: perturb one node's u_x in the
     given-gradient residual and difference Lv."""
-    prob = _with(fi.config1_tiny(), b=(0.4, 0.0), eps=0.6)
+    prob = _with(fi.tiny_square(), b=(0.4, 0.0), eps=0.6)
     b = oracle.Bound(prob, with_boundary=False)
     out = b.loss_grad(prob.params, want_ubar=True, want_upts=True)
     up = out["upts"].reshape(-1, 3)
@@ -416,7 +416,7 @@ def test_adjoint_seeds_are_dL_dgradu():
 
 
 def test_boundary_and_sensor_terms():
-    prob = fi.config4_inverse(4)
+    prob = fi.inverse_cd2d(4)
     out = oracle.Bound(prob).loss_grad(prob.params)
     u, _, _ = oracle.mlp(prob.widths, prob.params, prob.bd_xy)
     us, _, _ = oracle.mlp(prob.widths, prob.params, prob.sensor_xy)

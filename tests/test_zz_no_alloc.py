@@ -35,10 +35,10 @@ def api():
     return A
 
 
-@pytest.mark.parametrize("k,precision", [(1, "fp64"), (2, "fp32"), (2, "fp16")])
+@pytest.mark.parametrize("k,precision", [("tiny", "fp64"), ("disc", "fp32"), ("disc", "fp16")])
 def test_noalloc_matches_loss_grad_on_two_calls(api, k, precision):
     ctx = api.Context(0)
-    prob = fi.CONFIGS[k]()
+    prob = fi.WORKLOADS[k]()
     pb = api.problem_from_inputs(ctx, prob, precision)
     params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
     outs = []
@@ -64,7 +64,7 @@ def test_noalloc_matches_loss_grad_on_two_calls(api, k, precision):
 def test_noalloc_rejects_a_problem_larger_than_its_scratch(api):
     from paper_2404_12063_b300 import FVError, _native as N
     ctx = api.Context(0)
-    prob = fi.config4_inverse()                    # 1.6 million points: temporaries exceed the area
+    prob = fi.inverse_cd2d()                    # 1.6 million points: temporaries exceed the area
     pb = api.problem_from_inputs(ctx, prob, "fp32")
     params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
     grad = torch.empty_like(params)
