@@ -423,7 +423,7 @@ def poisson_batch(n_instances: int = 64, seed: int = 4) -> List[Problem]:
     return out
 
 
-def config_eps_field() -> Problem:
+def eps_field_disc() -> Problem:
     """Space-dependent diffusion (Sec. 4.7.2): -div(eps(x, y) grad u) + b . grad u = f
     on the skewed 1024-element disc (Q=8, T=6), f = 10, b = (1, 0); one
     network 2-30x3-2 with outputs (u, eps) (seed 5); 1000 boundary points with

@@ -376,6 +376,13 @@ def test_regular_mesh_matches_oracle(api, ctx, precision, nx, ny, Q, T, b, eps):
     check_against_oracle(api, ctx, prob, precision, g_mode="regular")
 
 
+def test_regular_mesh_full_size_matches_oracle(api, ctx):
+    """The size the contraction-forms benchmark times (65,536 elements,
+    Q = 10, T = 8): 512 element tiles, more than one per CTA."""
+    prob = _uniform_problem(256, 256, 10, 8, (0.0, 0.0), 1.0)
+    check_against_oracle(api, ctx, prob, "fp16", g_mode="regular")
+
+
 def test_regular_mesh_agrees_with_stored_g(api, ctx):
     prob = _uniform_problem(15, 20, 10, 8, (0.4, -0.3), 0.8)
     _, _, o_r, g_r = gpu_eval(api, ctx, prob, "fp16", g_mode="regular")
@@ -399,7 +406,7 @@ def test_regular_mode_fp32_uses_the_matrix_free_kernel(api, ctx):
 # ---------------------------------------------------------------- space-dependent eps (two-output network)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_eps_field_matches_oracle(api, ctx, precision):
-    out, grad, ref = check_against_oracle(api, ctx, fi.config_eps_field(), precision)
+    out, grad, ref = check_against_oracle(api, ctx, fi.eps_field_disc(), precision)
     assert out[4] == 0.0
 
 
@@ -449,7 +456,7 @@ def test_eps_field_constant_output_equals_scalar_eps(api, ctx):
 
 def test_eps_field_rejected_by_tensor_cores(api, ctx):
     from paper_2404_12063_b300 import FVError, _native as N
-    prob = fi.config_eps_field()
+    prob = fi.eps_field_disc()
     pb = api.problem_from_inputs(ctx, prob, "fp16", storage="fp32")
     params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
     with pytest.raises(FVError) as ei:
