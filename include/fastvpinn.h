@@ -170,13 +170,14 @@ int fv_mesh_set_g_mode(fv_mesh mesh, int mode);
 
 /* Autotune the contraction of Alg. 3 for this mesh at evaluation precision
  * `mlp_precision`: times each candidate launch plan (one or two shared-memory
- * stages per CTA, with the element grouping and lane splits the planner picks
- * for each) on zero-valued inputs and keeps the fastest in the mesh handle.
- * Later evaluations with this mesh and precision use it; without a call the
- * two-stage plan is used.  Plans differ only in how sums are grouped, so a
- * tuned and an untuned evaluation agree to rounding, and each plan is
- * deterministic.  ms_out (nullable, host, 2 doubles) receives the median
- * times of the two-stage and one-stage plans.
+ * stages per CTA, each with the planner's element grouping and with 1 to 4
+ * elements per stage; lane splits as the planner picks them) on zero-valued
+ * inputs and keeps the fastest in the mesh handle.  Later evaluations with
+ * this mesh and precision use it; without a call the planner's two-stage
+ * plan is used.  Plans differ only in how sums are grouped, so a tuned and an
+ * untuned evaluation agree to rounding, and each plan is deterministic.
+ * ms_out (nullable, host, 2 doubles) receives the median times of the best
+ * two-stage and the best one-stage candidate.
  * Errors: FV_ERR_ARG (null mesh, precision not 0..4), FV_ERR_OOM, FV_ERR_CUDA.
  * Synchronises the stream; not allowed during stream capture. */
 int fv_autotune(fv_ctx ctx, fv_mesh mesh, fv_precision mlp_precision, double* ms_out);

@@ -15,6 +15,7 @@
 // vector loads of G and grad u) and the column pass (adjoint seeds; one
 // q-chunk per lane group) on the same shared tile.
 #include <algorithm>
+#include <vector>
 #include <cmath>
 #include <type_traits>
 
@@ -117,7 +118,14 @@ struct Aux {
 constexpr int kCThreads = 128;                      // staged kernel: 4 warps, several CTAs per SM
 constexpr int kCWarps = kCThreads / 32;
 
-__host__ __device__ inline size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+__host__ __device__ inline size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Values per element row of the staged u_x / u_y: N_q rounded up to the
+// vector width (at least 4), so that every q-chunk load is aligned.
+__host__ __device__ inline int aux_row(int Nq, int vec) {
+  const int a = vec > 4 ? vec : 4;
+  return (Nq + a - 1) / a * a;
+}
 
 // Shared-memory layout of the staged kernel (offsets in bytes); host and
 // device evaluate the same function.
@@ -130,10 +138,10 @@ __host__ __device__ inline StagedLayout staged_layout(int Eg, int Nt, int nqp, i
   StagedLayout L;
   const int ntp = (Nt + 7) & ~7;
   L.aux_n = (size_t)2 * Eg * nqp + (size_t)Eg * ntp;
-  L.rb = round128(2 * L.aux_n * rsz);                 // two aux buffers at offset 0
-  L.red = L.rb + round128((size_t)Eg * Nt * rsz);     // Rbar of the stage's rows
-  L.bar = L.red + round128(kCWarps * 4 * 8);          // per-warp loss partials
-  L.stage = L.bar + 128;                              // up to 16 stage barriers
+  L.rb = round16(2 * L.aux_n * rsz);                  // two aux buffers at offset 0
+  L.red = L.rb + round16((size_t)Eg * Nt * rsz);      // Rbar of the stage's rows
+  L.bar = L.red + round16(kCWarps * 4 * 8);           // per-warp loss partials
+  L.stage = L.bar + round16((size_t)S * 8);           // one barrier per stage; bulk copies land 16-byte aligned
   L.total = L.stage + (size_t)S * stage_bytes;
   return L;
 }
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Nt = CNT ? CNT : a.Nt, Nq = CNCH ? CNCH * VEC : a.Nq, Eg = a.elems_per_stage, S = a.n_stages;
   const int sh1 = CSH1 >= 0 ? CSH1 : a.sh1, sh2 = CSH2 >= 0 ? CSH2 : a.sh2, H1 = 1 << sh1, H2 = 1 << sh2;
-  const int nqp = CNCH ? ((CNCH * VEC + 7) & ~7) : a.nq_pad;
+  const int nqp = CNCH ? aux_row(CNCH * VEC, VEC) : a.nq_pad;
   const int lg_rpw = 5 - sh1;                         // rows per warp and round: 32 / H1
   const int nch = Nq / VEC;
   const size_t stage_bytes = (size_t)Eg * a.g_stride_bytes;
@@ -609,7 +617,7 @@ int gcd_int(int a, int b) { return b ? gcd_int(b, a % b) : a; }
 // where an element block is too large for two stages.  The row pass rotates each lane's
 // chunk order when the row length in chunks shares a factor with the number
 // of lanes that one shared-memory wavefront serves.
-ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages = 0) {
+ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages = 0, int elems = 0) {
   ContractPlan P;
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
   const size_t gsz = g_value_bytes(m->storage);
@@ -618,10 +626,12 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
   for (int v = 8; v >= 2; v >>= 1)
     if (v * gsz <= 16 && m->Nq % v == 0) { vec = v; break; }
   const int nch = m->Nq / vec;
-  const int nqp = (m->Nq + 7) & ~7;
+  const int nqp = aux_row(m->Nq, vec);
   const int wave_lanes = (int)std::min<size_t>(32, std::max<size_t>(1, 128 / (vec * gsz)));
-  const int tuned = m->contract_stages[prec == FV_FP64 ? 1 : 0];
+  const int slot = prec == FV_FP64 ? 1 : 0;
+  const int tuned = m->contract_stages[slot];
   const int S = stages ? stages : tuned ? tuned : 2;
+  const int Ef = stages ? elems : m->contract_elems[slot];     // forced elements per stage (0: by the model)
   const size_t max_ctas = S == 1 ? 8 : 4;
   double best = 1e300;
   for (int E = 1; E <= 16 && E <= m->n_e; ++E) {
@@ -629,6 +639,7 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
     if (L.total > ctx->smem_optin || E * gs > (1u << 20) - 16) break;
     const int C = (int)std::min<size_t>(max_ctas, ctx->smem_per_sm / (L.total + 1024));
     if (C < 1) break;
+    if (Ef && E != Ef) continue;
     double c1 = 1e300, c2 = 1e300;
     int s1 = 0, s2 = 0;
     for (int sh = 0; sh <= 3 && (1 << sh) <= nch; ++sh) {
@@ -652,7 +663,7 @@ ContractPlan plan_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, int stages 
       P.grid = std::min<int>((m->n_e + E - 1) / E, ctx->n_sm * C);
     }
   }
-  if (!P.staged && S == 2 && !stages) return plan_contract(ctx, m, prec, 1);   // one stage per CTA
+  if (!P.staged && S == 2 && !stages) return plan_contract(ctx, m, prec, 1, Ef);   // one stage per CTA
   if (!P.staged) {        // an element too large to stage: direct kernel
     P.smem = (size_t)m->Nt * 8 + kWarps * 4 * 8;
     P.grid = (int)std::min<int64_t>(m->n_e, (int64_t)ctx->n_sm * 8);
@@ -680,14 +691,25 @@ int contract_grid(fv_ctx ctx, fv_mesh m, fv_precision prec, int* grid, int* eg, 
   return FV_OK;
 }
 
-// Times the one- and two-stage plans on zero-valued inputs (median of seven
-// launches after two warm-up launches each) and keeps the faster one.
+// Times candidate plans on zero-valued inputs (median of seven launches after
+// two warm-up launches each) and keeps the fastest: one and two stages per CTA,
+// each with the cost model's elements per stage and with 1 to 4 elements.
 int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) {
   const int slot = prec == FV_FP64 ? 1 : 0;
   const size_t rsz = prec == FV_FP64 ? 8 : 4;
-  const ContractPlan p2 = plan_contract(ctx, m, prec, 2), p1 = plan_contract(ctx, m, prec, 1);
   if (ms_out) ms_out[0] = ms_out[1] = 0.0;
-  if (!p2.staged || !p1.staged || m->g_mode != FV_G_STORED) return FV_OK;   // nothing to choose
+  if (m->g_mode != FV_G_STORED) return FV_OK;
+  struct Cand { int S, E, grid; };
+  std::vector<Cand> cands;
+  for (int S = 2; S >= 1; --S)
+    for (int E = 0; E <= 4; ++E) {
+      const ContractPlan p = plan_contract(ctx, m, prec, S, E);
+      if (!p.staged || p.S != S) continue;
+      bool dup = false;
+      for (const Cand& c : cands) dup |= c.S == S && c.E == p.E;
+      if (!dup) cands.push_back({S, p.E, p.grid});
+    }
+  if (cands.size() < 2) return FV_OK;   // nothing to choose
   EvalPlan pl;
   pl.prec = prec;
   pl.P_mesh = pl.P_tot = m->P;
@@ -695,9 +717,11 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
   pl.shape.w[0] = 2;
   pl.shape.w[1] = 1;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  int max_grid = 1;
+  for (const Cand& c : cands) max_grid = std::max(max_grid, c.grid);
   const size_t u_bytes = 3 * (size_t)m->P * rsz, nf = (size_t)m->n_e * m->Nt;
   const size_t o_ub = al(u_bytes), o_f = o_ub + al(u_bytes), o_f32 = o_f + al(nf * 8), o_part = o_f32 + al(nf * 4);
-  const size_t total = o_part + al((size_t)std::max(p1.grid, p2.grid) * 16);
+  const size_t total = o_part + al((size_t)max_grid * 16);
   char* buf = nullptr;
   if (cudaMalloc(&buf, total) != cudaSuccess) {
     cudaGetLastError();
@@ -719,12 +743,14 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
   if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   if (ce != cudaSuccess) fail(ce);
-  const int saved = m->contract_stages[slot];
+  const int saved_s = m->contract_stages[slot], saved_e = m->contract_elems[slot];
   const bool timing = ctx->timing;
   ctx->timing = false;
-  double med[2] = {0.0, 0.0};
-  for (int pass = 0; pass < 2 && rc == FV_OK; ++pass) {
-    m->contract_stages[slot] = pass == 0 ? 2 : 1;
+  double best_ms = 1e300, best_s[3] = {0.0, 1e300, 1e300};
+  int best = -1;
+  for (size_t k = 0; k < cands.size() && rc == FV_OK; ++k) {
+    m->contract_stages[slot] = cands[k].S;
+    m->contract_elems[slot] = cands[k].E;
     float t[7] = {0};
     int n_part = 0;
     for (int r = 0; r < 9 && rc == FV_OK; ++r) {
@@ -737,18 +763,21 @@ int autotune_contract(fv_ctx ctx, fv_mesh m, fv_precision prec, double* ms_out) 
     }
     if (rc == FV_OK) {
       std::sort(t, t + 7);
-      med[pass] = t[3];
+      const double ms = t[3];
+      best_s[cands[k].S] = std::min(best_s[cands[k].S], ms);
+      if (ms < best_ms) { best_ms = ms; best = (int)k; }
     }
   }
   ctx->timing = timing;
   if (rc == FV_OK && (ce = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) fail(ce);
-  m->contract_stages[slot] = rc == FV_OK ? (med[1] < med[0] ? 1 : 2) : saved;
+  m->contract_stages[slot] = rc == FV_OK && best >= 0 ? cands[best].S : saved_s;
+  m->contract_elems[slot] = rc == FV_OK && best >= 0 ? cands[best].E : saved_e;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(buf);
   if (ms_out && rc == FV_OK) {
-    ms_out[0] = med[0];
-    ms_out[1] = med[1];
+    ms_out[0] = best_s[2] < 1e300 ? best_s[2] : 0.0;
+    ms_out[1] = best_s[1] < 1e300 ? best_s[1] : 0.0;
   }
   return rc;
 }

@@ -96,6 +96,7 @@ struct fv_mesh_s {
   int* cells = nullptr;             // [n_e][4]
   int n_v = 0;
   int contract_stages[2] = {0, 0};  // tuned stages per CTA (FP32 / FP64 evaluation); 0 = default
+  int contract_elems[2] = {0, 0};   // tuned elements per stage (FP32 / FP64 evaluation); 0 = the planner's choice
   int g_mode = FV_G_STORED;         // contraction from the stored G or matrix-free
   float* jreg = nullptr;            // regular mode: per element y_eta, x_xi, |J| (FP32), [n_e][3]
 };
