@@ -99,6 +99,7 @@ struct fv_mesh_s {
   int contract_elems[2] = {0, 0};   // tuned elements per stage (FP32 / FP64 evaluation); 0 = the planner's choice
   int g_mode = FV_G_STORED;         // contraction from the stored G or matrix-free
   float* jreg = nullptr;            // regular mode: per element y_eta, x_xi, |J| (FP32), [n_e][3]
+  void* reg_ref[2] = {nullptr, nullptr};   // regular mode: FP16 / BF16 shared-memory images of the reference matrix
 };
 
 struct fv_forcing_s {
@@ -232,6 +233,7 @@ void mfree_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* war
 bool regular_supported(fv_mesh mesh, fv_precision prec);
 int regular_grid(fv_ctx ctx, fv_mesh mesh);
 int check_regular_mesh(fv_mesh mesh, std::vector<float>* scales);
+int build_regular_reference(fv_mesh mesh);
 int launch_contract_regular(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U,
                             void* UB, double eps, const double* eps_dev, double bx, double by, double rscale,
                             double* partials, int* n_partials_out, double* R_out);

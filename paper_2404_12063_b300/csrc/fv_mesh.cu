@@ -306,6 +306,7 @@ extern "C" int fv_mesh_destroy(fv_mesh m) {
   clear_error();
   if (!m) return FV_OK;
   cudaFree(m->G); cudaFree(m->X); cudaFree(m->tables); cudaFree(m->verts); cudaFree(m->cells); cudaFree(m->jreg);
+  cudaFree(m->reg_ref[0]); cudaFree(m->reg_ref[1]);
   delete m;
   return FV_OK;
 }
@@ -322,6 +323,8 @@ extern "C" int fv_mesh_set_g_mode(fv_mesh m, int mode) {
     if (rc) return rc;
     if (!m->jreg) FV_CUDA_TRY(cudaMalloc(&m->jreg, sizeof(float) * 3 * (size_t)m->n_e));
     FV_CUDA_TRY(cudaMemcpy(m->jreg, scales.data(), sizeof(float) * scales.size(), cudaMemcpyHostToDevice));
+    const int rb = build_regular_reference(m);
+    if (rb) return rb;
   }
   m->g_mode = mode;
   return FV_OK;

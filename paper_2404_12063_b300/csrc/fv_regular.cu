@@ -6,17 +6,16 @@
 //   Vxi = w v_xi,  Veta = w v_eta,  V = w v  (reference, shared by all elements)
 //   J_x = |J| / (dx/dxi)... = h_y / 2,  J_y = h_x / 2,  J = h_x h_y / 4
 //
-// so the residuals of a tile of 128 elements are one GEMM with N = elements,
+// so the residuals of a tile of 128 elements are GEMMs with N = elements,
 //
-//   D1 [N_t x 128] = [Vxi | Veta (| V)] . [eps J_x u_x ; eps J_y u_y (; J (b . grad u))]
-//   R = D1 - F^T,  Lv = inv_norm sum R^2,  Rbar = rscale R
+//   A [N_t x 128] = [Vxi | Veta] . [J_x u_x ; J_y u_y],   B = V . [J (b . grad u)]  (convection)
+//   R = eps A + B - F^T,  Lv = inv_norm sum R^2,  Rbar = rscale R,  dL/deps = sum Rbar A
 //
 // and the adjoint seeds three more, D2_c [N_q x 128] = V_c^T . Rbar:
 //
-//   dL/du_x = eps J_x D2_xi + bx J D2_v,  dL/du_y = eps J_y D2_eta + by J D2_v,
-//   dL/deps = sum (J_x u_x D2_xi + J_y u_y D2_eta).
+//   dL/du_x = eps J_x D2_xi + bx J D2_v,  dL/du_y = eps J_y D2_eta + by J D2_v.
 //
-// All four run on the tensor cores (tcgen05, 16-bit operands, FP32
+// All of them run on the tensor cores (tcgen05, 16-bit operands, FP32
 // accumulators in tensor memory).  The reference matrix is stored once in
 // shared memory in the core-matrix layout and read K-major (rows = tests) by
 // the residual GEMM and MN-major (rows = quadrature points) by the adjoint
@@ -41,13 +40,14 @@ struct RegPlan {
   int Nq_pad;        // K-block width per component: Nq rounded up to 16
   int M2;            // adjoint GEMMs' M (64 or 128 >= Nq); reads may run into the next block (rows >= Nq unused)
   int Nt_blk, K1, nc;
-  int o_A, o_B1, o_B2, o_J, o_tab, o_red, o_bar, smem;
+  int o_A, o_B1, o_B2, o_J, o_red, o_bar, smem;
   int tmem_cols;
 };
 
 struct RegArgs {
   RegPlan pl;
   const float* J;         // [n_e][3]: y_eta, x_xi, |J| (rectangles)
+  const uint4* ref;       // the reference matrix as its shared-memory image (Nt_blk x K1 16-bit values)
   const double* tables;   // xi[Q], w[Q], v[T][Q], dv[T][Q]
   int n_e, Q, T;
   const float* F;         // [n_e][T*T]
@@ -75,7 +75,6 @@ bool make_reg_plan(int Q, int T, int nc, RegPlan* p) {
   p->o_B1 = o; o += kRegTile * p->K1 * 2;          // B1 follows A: the adjoint reads past A's last block land here
   p->o_B2 = o; o += kRegTile * p->Nt_blk * 2;
   p->o_J = o; o += kRegTile * 3 * 4;                 // per element J_x, J_y, J
-  p->o_tab = o; o += (Q + 2 * T * Q) * 4;            // FP32 w[Q], v[T][Q], dv[T][Q] (prologue)
   o = (o + 15) & ~15;
   p->o_red = o; o += 64 * 8;                         // max |Rbar| bits, loss partials
   p->o_bar = o; o += 16;                             // mbarrier + TMEM base
@@ -97,6 +96,31 @@ __device__ __forceinline__ uint16_t to16(float v) {
   return (uint16_t)(OP::pack(v, 0.f) & 0xFFFFu);
 }
 
+// The reference matrix [Vxi | Veta (| V)] in the core-matrix image of the
+// kernel's A operand: row j = (m, n) per CTA, columns c Nq_pad + q with q = (a, b);
+// products of the one-dimensional tables in FP32, rounded to 16 bits.
+template <class OP>
+__global__ void __launch_bounds__(128) build_reference(const double* __restrict__ tables, int Q, int T, int Nqb,
+                                                       int K1, uint16_t* __restrict__ out) {
+  const int j = blockIdx.x, Nt = T * T, Nq = Q * Q;
+  const double* w = tables + Q;
+  const double* v = w + Q;
+  const double* dv = v + T * Q;
+  const bool jv = j < Nt;
+  const int m = jv ? j / T : 0, n = jv ? j - m * T : 0;
+  for (int k = threadIdx.x; k < K1; k += blockDim.x) {
+    const int c = k / Nqb, q = k - c * Nqb;
+    float val = 0.f;
+    if (jv && q < Nq) {
+      const int ia = q / Q, ib = q - ia * Q;
+      const float r = c == 0 ? (float)dv[m * Q + ia] * (float)v[n * Q + ib]
+                    : c == 1 ? (float)v[m * Q + ia] * (float)dv[n * Q + ib] : (float)v[m * Q + ia] * (float)v[n * Q + ib];
+      val = ((float)w[ia] * (float)w[ib]) * r;
+    }
+    out[cm_off(j, k, K1) >> 1] = to16<OP>(val);
+  }
+}
+
 template <class OP, int NC>
 __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -116,33 +140,19 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // reference matrix [Vxi | Veta (| V)]: rows j = (m, n), columns c Nq_pad + q, q = (a, b);
-  // products of the one-dimensional tables in FP32 (the entries are rounded to 16 bits)
+  // the reference matrix, built once per mesh in its shared-memory image: 16-byte copies
   {
-    float* tw = reinterpret_cast<float*>(sm + pl.o_tab);
-    float* tv = tw + Q;
-    float* tdv = tv + T * Q;
-    for (int i = tid; i < Q + 2 * T * Q; i += kRegThreads) tw[i] = (float)a.tables[Q + i];
-    __syncthreads();
-    for (int idx = tid; idx < Ntb * K1; idx += kRegThreads) {
-      const int j = idx / K1, k = idx - j * K1;
-      const int c = k / Nqb, q = k - c * Nqb;
-      float val = 0.f;
-      if (j < Nt && q < Nq) {
-        const int m = j / T, n = j - m * T, ia = q / Q, ib = q - ia * Q;
-        const float r = c == 0 ? tdv[m * Q + ia] * tv[n * Q + ib]
-                      : c == 1 ? tv[m * Q + ia] * tdv[n * Q + ib] : tv[m * Q + ia] * tv[n * Q + ib];
-        val = (tw[ia] * tw[ib]) * r;
-      }
-      *reinterpret_cast<uint16_t*>(sA + cm_off(j, k, K1)) = to16<OP>(val);
-    }
+    const int n16 = Ntb * K1 * 2 / 16;
+    for (int i = tid; i < n16; i += kRegThreads) reinterpret_cast<uint4*>(sA)[i] = a.ref[i];
   }
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tD = *s_tmem;
-  const uint32_t tD1 = tD, tD2 = tD;                  // D2_c at columns 128 c (D1 is dead by then)
+  // D1 (diffusion residual A) at columns 0..127, the convection residual (three
+  // components) at 384..511; D2_c at columns 128 c (D1 is dead by then)
+  const uint32_t tD1 = tD, tD1c = tD + 3 * kRegTile, tD2 = tD;
   const float eps = (float)(a.eps_d ? *a.eps_d : a.eps_h);
   const float bx = (float)a.bx, by = (float)a.by, rscale = (float)a.rscale;
   uint32_t phase = 0;
@@ -185,8 +195,8 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
         for (int r = 0; r < 4; ++r) {
           const int q = lane + 32 * r;
           if (q >= Nqb) continue;
-          *reinterpret_cast<uint16_t*>(sB1 + cm_off(n, q, K1)) = to16<OP>(eps * jx * ux[t][r]);
-          *reinterpret_cast<uint16_t*>(sB1 + cm_off(n, Nqb + q, K1)) = to16<OP>(eps * jy * uy[t][r]);
+          *reinterpret_cast<uint16_t*>(sB1 + cm_off(n, q, K1)) = to16<OP>(jx * ux[t][r]);
+          *reinterpret_cast<uint16_t*>(sB1 + cm_off(n, Nqb + q, K1)) = to16<OP>(jy * uy[t][r]);
           if (NC == 3)
             *reinterpret_cast<uint16_t*>(sB1 + cm_off(n, 2 * Nqb + q, K1)) =
                 to16<OP>(jj * (bx * ux[t][r] + by * uy[t][r]));
@@ -201,10 +211,12 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
     if (tid == 0) {
       tc_fence_after();
       const uint32_t id = idesc_f16(OP::fmt, Ntb, kRegTile, 0, 0);
+      const int kd = 2 * Nqb / 16;                    // K steps of the two diffusion components
       for (int kk = 0; kk < K1 / 16; ++kk) {
         const uint64_t ad = sdesc(su32(sA) + kk * 256, 128, K1 * 16);
         const uint64_t bd = sdesc(su32(sB1) + kk * 256, 128, K1 * 16);
-        mma_bf16(tD1, ad, bd, id, kk > 0);
+        if (kk < kd) mma_bf16(tD1, ad, bd, id, kk > 0);
+        else mma_bf16(tD1c, ad, bd, id, kk > kd);
       }
       mma_commit(bar);
     }
@@ -216,20 +228,24 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
     //      their F entries loaded together
     float rmax = 0.f;
     for (int c = c_lo; c < c_hi; c += 16) {
-      float d[16], fv[16];
+      float d[16], dc[16], fv[16];
       const bool rv = row1 >= 0 && row1 < Nt;
 #pragma unroll
       for (int i = 0; i < 16; ++i) fv[i] = rv && e0 + c + i < a.n_e ? a.F[(size_t)(e0 + c + i) * Nt + row1] : 0.f;
 #pragma unroll
-      for (int i = 0; i < 16; i += 8) tmem_ld8(tD1 + tRow + c + i, d + i);
+      for (int i = 0; i < 16; i += 8) {
+        tmem_ld8(tD1 + tRow + c + i, d + i);
+        if (NC == 3) tmem_ld8(tD1c + tRow + c + i, dc + i);
+      }
       tmem_wait_ld();
       if (rv) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int e = e0 + c + i;
           if (e < a.n_e) {
-            const float R = d[i] - fv[i];
+            const float R = fmaf(eps, d[i], (NC == 3 ? dc[i] : 0.f) - fv[i]);   // eps A + B - F
             lt = fmaf(R, R, lt);
+            dt = fmaf(rscale * R, d[i], dt);                                       // Rbar A
             rmax = fmaxf(rmax, fabsf(rscale * R));
             if (a.R_out) a.R_out[(size_t)e * Nt + row1] = (double)R;
           }
@@ -251,18 +267,22 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
     }
     // pass B: Rbar s into B2 (rows = elements, K = tests); invalid rows and columns are zero
     for (int c = c_lo; c < c_hi; c += 16) {
-      float d[16], fv[16];
+      float d[16], dc[16], fv[16];
       const bool rv = row1 >= 0 && row1 < Nt;
 #pragma unroll
       for (int i = 0; i < 16; ++i) fv[i] = rv && e0 + c + i < a.n_e ? a.F[(size_t)(e0 + c + i) * Nt + row1] : 0.f;
 #pragma unroll
-      for (int i = 0; i < 16; i += 8) tmem_ld8(tD1 + tRow + c + i, d + i);
+      for (int i = 0; i < 16; i += 8) {
+        tmem_ld8(tD1 + tRow + c + i, d + i);
+        if (NC == 3) tmem_ld8(tD1c + tRow + c + i, dc + i);
+      }
       tmem_wait_ld();
       if (row1 >= 0) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int e = e0 + c + i;
-          const float rb = rv && e < a.n_e ? sc * rscale * (d[i] - fv[i]) : 0.f;
+          const float R = fmaf(eps, d[i], (NC == 3 ? dc[i] : 0.f) - fv[i]);
+          const float rb = rv && e < a.n_e ? sc * rscale * R : 0.f;
           *reinterpret_cast<uint16_t*>(sB2 + cm_off(c + i, row1, Ntb)) = to16<OP>(rb);
         }
       }
@@ -292,18 +312,11 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
     phase ^= 1;
     if (__syncthreads_or(!ok)) { failed = true; if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); break; }
     tc_fence_after();
-    // ---- epilogue 2: seeds and the eps derivative, 8 elements at a time
+    // ---- epilogue 2: the seeds, 8 elements at a time
     const float inv = 1.f / sc;
     const bool qv = row2 >= 0 && row2 < Nq;
     for (int c = c_lo; c < c_hi; c += 8) {
-      float dx[8], dy[8], dvv[8], ux[8], uy[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool in = qv && e0 + c + i < a.n_e;
-        const int64_t p = (int64_t)(e0 + c + i) * Nq + row2;
-        ux[i] = in ? a.U[a.P_tot + p] : 0.f;
-        uy[i] = in ? a.U[2 * a.P_tot + p] : 0.f;
-      }
+      float dx[8], dy[8], dvv[8];
       tmem_ld8(tD2 + tRow + c, dx);
       tmem_ld8(tD2 + kRegTile + tRow + c, dy);
       if (NC == 3) tmem_ld8(tD2 + 2 * kRegTile + tRow + c, dvv);
@@ -316,7 +329,6 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
           const float jx = sJ[n * 3], jy = sJ[n * 3 + 1], jj = sJ[n * 3 + 2];
           const float sx = dx[i] * inv, sy = dy[i] * inv, sv = NC == 3 ? dvv[i] * inv : 0.f;
           const int64_t p = (int64_t)e * Nq + row2;
-          dt += jx * ux[i] * sx + jy * uy[i] * sy;
           a.UB[p] = 0.f;
           a.UB[a.P_tot + p] = eps * jx * sx + bx * jj * sv;
           a.UB[2 * a.P_tot + p] = eps * jy * sy + by * jj * sv;
@@ -401,6 +413,37 @@ int check_regular_mesh(fv_mesh m, std::vector<float>* scales) {
   return FV_OK;
 }
 
+// The FP16 and BF16 images of the reference matrix for this mesh's orders
+// (nothing to build where the GEMM form does not apply).
+int build_regular_reference(fv_mesh m) {
+  RegPlan p;
+  if (!make_reg_plan(m->Q, m->T, m->n_comp, &p)) return FV_OK;
+  const size_t bytes = (size_t)p.Nt_blk * p.K1 * 2;
+  for (int img = 0; img < 2; ++img) {
+    if (!m->reg_ref[img]) {
+      const cudaError_t e = cudaMalloc(&m->reg_ref[img], bytes);
+      if (e != cudaSuccess) {
+        set_error("fv_mesh_set_g_mode: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;
+      }
+    }
+    uint16_t* out = static_cast<uint16_t*>(m->reg_ref[img]);
+    if (img == 0) build_reference<OpF16><<<p.Nt_blk, 128, 0, m->ctx->stream>>>(m->tables, m->Q, m->T, p.Nq_pad, p.K1, out);
+    else build_reference<OpBF16><<<p.Nt_blk, 128, 0, m->ctx->stream>>>(m->tables, m->Q, m->T, p.Nq_pad, p.K1, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error("fv_mesh_set_g_mode: reference build failed: %s", cudaGetErrorString(e));
+      return FV_ERR_CUDA;
+    }
+  }
+  const cudaError_t e = cudaStreamSynchronize(m->ctx->stream);
+  if (e != cudaSuccess) {
+    set_error("fv_mesh_set_g_mode: %s", cudaGetErrorString(e));
+    return FV_ERR_CUDA;
+  }
+  return FV_OK;
+}
+
 int launch_contract_regular(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, const void* U, void* UB,
                             double eps, const double* eps_dev, double bx, double by, double rscale,
                             double* partials, int* n_part, double* R_out) {
@@ -413,7 +456,12 @@ int launch_contract_regular(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan&
     set_error("regular-mesh contraction: the mesh has no element scales (set FV_G_REGULAR first)");
     return FV_ERR_ARG;
   }
-  a.J = m->jreg; a.tables = m->tables;
+  const int img = pl.prec == FV_FP16 ? 0 : 1;
+  if (!m->reg_ref[img]) {
+    set_error("regular-mesh contraction: the mesh has no reference matrix (set FV_G_REGULAR first)");
+    return FV_ERR_ARG;
+  }
+  a.J = m->jreg; a.tables = m->tables; a.ref = static_cast<const uint4*>(m->reg_ref[img]);
   a.n_e = m->n_e; a.Q = m->Q; a.T = m->T;
   a.F = f->F32;
   a.U = static_cast<const float*>(U); a.UB = static_cast<float*>(UB); a.P_tot = pl.P_tot;
