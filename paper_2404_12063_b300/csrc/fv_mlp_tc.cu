@@ -91,12 +91,25 @@ __device__ void tc_load_weights(const TcPlan& pl, const float* __restrict__ P, u
     const int in = pl.w[i], out = pl.w[i + 1], Kb = pl.WP[i - 1], Nr = pl.WP[i];
     const float* W = P + pl.off[i];
     uint16_t* dst = reinterpret_cast<uint16_t*>(sm + pl.o_w[i]);
-    for (int idx = threadIdx.x; idx < Nr * Kb; idx += blockDim.x) {
-      const int o = idx / Kb, k = idx - o * Kb;
-      float v = 0.f;
-      if (o < out) v = k < in ? W[o * in + k] : (k == in ? W[out * in + o] : 0.f);
-      const uint32_t byte = row_off(o, Kb) + (k >> 3) * 128 + (k & 7) * 2;
-      dst[byte >> 1] = (uint16_t)(OP::pack(v, 0.f) & 0xFFFFu);
+    // eight entries per thread and pass, all loads issued before the first use
+    constexpr int U = 8;
+    for (int base = threadIdx.x; base < Nr * Kb; base += U * blockDim.x) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * blockDim.x;
+        const int o = idx / Kb, k = idx - o * Kb;
+        v[u] = 0.f;
+        if (idx < Nr * Kb && o < out) v[u] = k < in ? W[o * in + k] : (k == in ? W[out * in + o] : 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx >= Nr * Kb) break;
+        const int o = idx / Kb, k = idx - o * Kb;
+        const uint32_t byte = row_off(o, Kb) + (k >> 3) * 128 + (k & 7) * 2;
+        dst[byte >> 1] = (uint16_t)(OP::pack(v[u], 0.f) & 0xFFFFu);
+      }
     }
   }
   float* s = reinterpret_cast<float*>(sm + pl.o_small);
