@@ -297,7 +297,7 @@ int check_eval(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_
 }
 
 struct WsLayout {
-  size_t U, UB, cpart, bcpart, gpart, smax, total;
+  size_t U, UB, cpart, bcpart, gpart, smax, ctr, total;
 };
 
 // The core evaluation shared by fv_loss, fv_loss_grad and fv_inverse_step.
@@ -350,6 +350,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   w.bcpart = o; o += al(2 * 8);
   w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
   w.smax = o; o += al(16);
+  w.ctr = o; o += al(16);
   w.total = o;
   if (ws_bytes_only) {          // size query only: nothing is launched
     *ws_bytes_only = w.total;
@@ -373,9 +374,11 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   double* bcpart = reinterpret_cast<double*>(b + w.bcpart);
   double* gpart = reinterpret_cast<double*>(b + w.gpart);
   float* smax = reinterpret_cast<float*>(b + w.smax);
+  int* tile_ctr = reinterpret_cast<int*>(b + w.ctr);
   const double* Xe = bc ? bc->xy : nullptr;
 
-  rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U) : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
+  rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U, tile_ctr)
+          : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
   if (rc) return rc;
   const double inv_norm = 1.0 / (opts->norm == FV_NORM_TEST ? mesh->Nt : mesh->n_e);
   int ncp = 0;

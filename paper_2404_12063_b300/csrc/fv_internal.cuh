@@ -252,7 +252,8 @@ int launch_finalize(fv_ctx ctx, const EvalPlan& pl, const double* cpart, int n_c
 
 // Tensor-core MLP paths (tcgen05).
 int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
-                      const double* Xextra, void* U);
+                      const double* Xextra, void* U,
+                      int* tile_counter);
 int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
                       const double* Xextra, const void* UB, double* gpart, int* n_blocks_out,
                       const float* seed_absmax);

@@ -50,7 +50,7 @@ struct TcPlan {
   int o_z;                  // adjoint tile (reverse kernel)
   int o_x;                  // layer-0 input tile (reverse kernel): 3 streams x 128 x 16
   int o_red;                // FP32 scratch [128][4] (output-layer partial sums)
-  int o_bar;                // mbarrier (8 B) + TMEM base (4 B) + flags (4 B)
+  int o_bar;                // mbarrier (8 B) + TMEM base (4 B) + flags (4 B) + two upcoming tile indices (8 B)
   int smem;
   int tmem_cols;
   int c_wbar[kMaxLayers];   // TMEM column of the weight-gradient accumulator of map i (reverse)
@@ -67,6 +67,7 @@ struct TcArgs {
   const float* UB;          // [3][P_tot] seeds (reverse)
   double* gpart;            // [grid][n_params] (reverse)
   const float* seed_absmax; // device max |seed| (FP16 reverse sweep) or null
+  int* tile_ctr;            // forward: tiles handed out beyond the first one per CTA (zero at launch)
   int* err;
 };
 
@@ -230,7 +231,7 @@ __device__ __forceinline__ void issue_wbar0(uint32_t fmt, uint32_t tW, uint32_t 
 // One activation tile, updated in place: once map i's MMAs have completed,
 // H_{i-1} is dead and the epilogue overwrites it with H_i.
 template <int HP, class OP>
-__global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
+__global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc(TcArgs a) {
   constexpr int NG = HP / 16;
   extern __shared__ __align__(1024) uint8_t sm[];
   const TcPlan& pl = a.pl;
@@ -248,6 +249,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // Tiles: the first from the CTA index, the later ones from the launch's
+  // counter (the outputs of a tile do not depend on which CTA computes it),
+  // requested two ahead so that the atomic and the next tile's coordinate
+  // loads are in flight during a tile; a ring of two shared slots.
+  int* s_tl = reinterpret_cast<int*>(sm + pl.o_bar + 16);
+  if (tid == 0) s_tl[0] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);
   tc_load_weights<OP>(pl, a.params, sm);
   fence_proxy_async();
   tc_fence_before();
@@ -261,10 +268,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
   const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
   PointIn nxt;                                  // next tile's coordinates, loads in flight
   if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
-  for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+  int64_t tile = blockIdx.x, next = s_tl[0];
+  for (int it = 0; tile < n_tiles && !failed; ++it) {
     const int64_t gp = tile * kTile + p;
     const float x = (float)nxt.x, y = (float)nxt.y;
-    if (tile + gridDim.x < n_tiles) point_fetch(a, (tile + gridDim.x) * kTile + p, nxt);
+    if (next < n_tiles) point_fetch(a, next * kTile + p, nxt);
+    if (tid == 0) s_tl[(it + 1) & 1] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);   // the tile after next
     float u = 0.f, ux = 0.f, uy = 0.f;          // output-layer partial sums over this thread's columns
     if (L == 2) {   // one hidden layer: output straight from layer 0
       for (int o = c0; o < min(pl.w[1], c0 + 16); ++o) {
@@ -353,6 +362,8 @@ __global__ void __launch_bounds__(tc_threads<HP>(), 2) mlp_fwd_tc(TcArgs a) {
       a.U[2 * a.P_tot + gp] = sy;
     }
     __syncthreads();
+    tile = next;
+    next = s_tl[(it + 1) & 1];
   }
   tc_fence_before();
   __syncthreads();
@@ -736,7 +747,7 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
     p->o_z = p->o_x = 0;
   }
   p->o_red = o; o += kTile * (HP / 16) * 3 * 4;
-  p->o_bar = o; o += 16;
+  p->o_bar = o; o += 32;
   p->smem = (o + 127) & ~127;
   int cols = 3 * HP;
   if (reverse) {
@@ -804,13 +815,19 @@ int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl) {
 }
 
 int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xm, const double* Xe,
-                      void* U) {
+                      void* U, int* tile_counter) {
   TcArgs a;
   if (!make_tc_plan(pl, false, &a.pl)) { set_error("tensor-core path: unsupported network"); return FV_ERR_UNSUPPORTED; }
   a.params = static_cast<const float*>(params);
   a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot;
   a.U = static_cast<float*>(U); a.UB = nullptr; a.gpart = nullptr; a.seed_absmax = nullptr; a.err = ctx->err_dev;
+  a.tile_ctr = tile_counter;
   const int grid = tc_grid(ctx, a.pl, false, pl.prec == FV_FP16, pl.P_tot);
+  cudaError_t e = cudaMemsetAsync(tile_counter, 0, sizeof(int), ctx->stream);
+  if (e != cudaSuccess) {
+    set_error("tensor-core forward: %s", cudaGetErrorString(e));
+    return FV_ERR_CUDA;
+  }
   cudaEvent_t ta;
   time_begin(ctx, K_MLP_FWD_TC, &ta);
   const int rc = launch_tc_any(ctx, a, false, pl.prec == FV_FP16, grid);
@@ -826,6 +843,7 @@ int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const 
   a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot;
   a.U = nullptr; a.UB = static_cast<const float*>(UB); a.gpart = gpart; a.err = ctx->err_dev;
   a.seed_absmax = pl.prec == FV_FP16 ? seed_absmax : nullptr;
+  a.tile_ctr = nullptr;
   const int grid = mlp_bwd_tc_blocks(ctx, pl);
   *nb = grid;
   cudaEvent_t ta;
