@@ -164,16 +164,30 @@ __global__ void __launch_bounds__(256) bc_kernel(const double* __restrict__ val,
   __shared__ double red[256];
   R lb = 0, ls = 0;
   const R cb = (R)(2.0 * tau / (n_bd > 0 ? n_bd : 1)), cs = (R)(2.0 * gamma / (n_s > 0 ? n_s : 1));
-  for (int d = threadIdx.x; d < n_bd + n_s; d += blockDim.x) {
-    const int64_t gp = P_mesh + d;
-    const R diff = U[gp] - (R)val[d];
-    R seed;
-    if (d < n_bd) { lb += diff * diff; seed = cb * diff; }
-    else { ls += diff * diff; seed = cs * diff; }
-    if (UB) {
-      UB[gp] = seed;
-      UB[P_tot + gp] = (R)0;
-      UB[2 * P_tot + gp] = (R)0;
+  const int nd = n_bd + n_s;
+  for (int d0 = threadIdx.x; d0 < nd; d0 += 4 * blockDim.x) {
+    R uv[4];
+    double gv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {          // loads of four points first, then their terms in order
+      const int d = d0 + k * blockDim.x;
+      uv[k] = d < nd ? U[P_mesh + d] : (R)0;
+      gv[k] = d < nd ? val[d] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int d = d0 + k * blockDim.x;
+      if (d >= nd) break;
+      const int64_t gp = P_mesh + d;
+      const R diff = uv[k] - (R)gv[k];
+      R seed;
+      if (d < n_bd) { lb += diff * diff; seed = cb * diff; }
+      else { ls += diff * diff; seed = cs * diff; }
+      if (UB) {
+        UB[gp] = seed;
+        UB[P_tot + gp] = (R)0;
+        UB[2 * P_tot + gp] = (R)0;
+      }
     }
   }
   const double a = block_sum256((double)lb, red);
@@ -183,8 +197,9 @@ __global__ void __launch_bounds__(256) bc_kernel(const double* __restrict__ val,
 
 // Deterministic final sums: the gradient over per-CTA partials and the loss
 // scalars, both as fixed-shape trees.  out = (L, Lv, Lb, Ls, dL/deps).
-// Gradient: 8 threads per parameter, each summing a strided subset of the
-// partials, then a 3-level shuffle tree.
+// Gradient (blocks 0 .. gridDim-2): 8 threads per parameter, each summing a
+// strided subset of the partials in a fixed order (loads issued eight at a
+// time), then a 3-level shuffle tree.  Loss scalars: the last block.
 template <class R>
 __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ cpart, int n_cpart,
                                                        const double* __restrict__ bcpart,
@@ -192,18 +207,28 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict_
                                                        double inv_norm, double tau, double gamma, int n_bd, int n_s,
                                                        R* __restrict__ grad, double* __restrict__ out) {
   __shared__ double red[256];
-  if (grad) {
+  if (grad && blockIdx.x + 1 < gridDim.x) {
     const int sub = threadIdx.x & 7;
     const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
     double s = 0.0;
     if (i < n_params)
-      for (int b = sub; b < n_gpart; b += 8) s += gpart[(size_t)b * n_params + i];
+      for (int b0 = sub; b0 < n_gpart; b0 += 64) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int b = b0 + 8 * u;
+          t[u] = b < n_gpart ? gpart[(size_t)b * n_params + i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (b0 + 8 * u < n_gpart) s += t[u];
+      }
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     s += __shfl_xor_sync(0xffffffffu, s, 4);
     if (i < n_params && sub == 0) grad[i] = (R)s;
   }
-  if (blockIdx.x == 0) {
+  if (blockIdx.x + 1 == gridDim.x) {
     double l = 0.0, d = 0.0;
     for (int b = threadIdx.x; b < n_cpart; b += blockDim.x) { l += cpart[2 * b]; d += cpart[2 * b + 1]; }
     l = block_sum256(l, red);
@@ -225,9 +250,18 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict_
 // a power of two derived from it); non-negative floats order like their bits.
 __global__ void __launch_bounds__(256) seed_absmax_kernel(const float* __restrict__ UB, int64_t n,
                                                           float* __restrict__ out) {
+  // 16-byte loads, four in flight per thread (UB starts on a 256-byte boundary), then the tail
   float m = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(UB[i]));
+  const int64_t n4 = n / 4, stride = (int64_t)gridDim.x * blockDim.x;
+  const float4* U4 = reinterpret_cast<const float4*>(UB);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = i + u * stride < n4 ? U4[i + u * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = fmaxf(m, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+  }
+  for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) m = fmaxf(m, fabsf(UB[i]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
@@ -410,7 +444,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
     cudaEvent_t ts;
     time_begin(ctx, K_SEED_SCALE, &ts);
     FV_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(float), ctx->stream));
-    seed_absmax_kernel<<<ctx->n_sm * 2, 256, 0, ctx->stream>>>((const float*)UB, 3 * pl.P_tot, smax);
+    seed_absmax_kernel<<<ctx->n_sm * 4, 256, 0, ctx->stream>>>((const float*)UB, 3 * pl.P_tot, smax);
     time_end(ctx, K_SEED_SCALE, ts);
     FV_CUDA_TRY(cudaGetLastError());
   }
@@ -422,7 +456,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   cudaEvent_t ta;
   time_begin(ctx, K_FINALIZE, &ta);
   const double tau = bc ? bc->tau : 0.0, gamma = bc ? bc->gamma : 0.0;
-  const int fgrid = want_grad ? std::max(1, (sh.n_params + 31) / 32) : 1;
+  const int fgrid = (want_grad ? (sh.n_params + 31) / 32 : 0) + 1;     // gradient blocks + the loss block
   if (pl.prec == FV_FP64)
     finalize_kernel<double><<<fgrid, 256, 0, ctx->stream>>>(cpart, ncp, bcpart, gpart, ngp, sh.n_params, inv_norm, tau,
                                                             gamma, pl.n_bd, pl.n_s, (double*)grad, out);
