@@ -115,7 +115,7 @@ class Mesh:
     def autotune(self, precision="fp32") -> tuple:
         """Time the contraction's launch plans for this mesh at `precision`
         and keep the fastest (fv_autotune).  Returns the median milliseconds
-        of the two-stage and one-stage plans."""
+        of the best two-stage and the best one-stage candidate."""
         ms = (C.c_double * 2)()
         N.call("fv_autotune", self.ctx.h, self.h, _prec(precision), ms)
         return ms[0], ms[1]
@@ -404,7 +404,7 @@ def problem_from_inputs(ctx: Context, prob, precision="fp32", storage=None, norm
     """Build the library handles for a problem description with fields mesh
     (vertices, cells), quad_order, test_order, widths, f(x, y), bd_xy, bd_g,
     tau, sensor_xy, sensor_u, gamma, eps, b (duck-typed).  g_mode
-    ('stored' / 'matrix_free') sets the mesh's contraction mode."""
+    ('stored' / 'matrix_free' / 'regular') sets the mesh's contraction mode."""
     prec = _prec(precision)
     if storage is None:
         storage = "fp64" if prec == N.FV_FP64 else "fp32"
