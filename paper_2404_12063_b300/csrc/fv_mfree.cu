@@ -15,6 +15,8 @@
 // One warp per element; the tables sit in shared memory once per CTA.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "fv_internal.cuh"
 
 namespace fv {
@@ -61,10 +63,12 @@ __host__ __device__ inline int mf_table_values(int Q, int T) { return 2 * Q + 2 
 // EPSQ: eps(x, y) at every node (the second output of a two-output network,
 // Sec. 4.7.2) instead of the scalar eps; the kernel then also writes the seed
 // dL/deps(x_q) = u_x sum_j Rbar_j Gx[j][q] + u_y sum_j Rbar_j Gy[j][q].
-template <class R, int NC, bool EPSQ>
+// QC, TC > 0: the orders as compile-time constants (index arithmetic by
+// constants, loops unrolled); 0: the runtime orders.
+template <class R, int NC, bool EPSQ, int QC = 0, int TC = 0>
 __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int Q = a.Q, T = a.T, Nq = Q * Q, Nt = T * T, TQ = T * Q;
+  const int Q = QC ? QC : a.Q, T = TC ? TC : a.T, Nq = Q * Q, Nt = T * T, TQ = T * Q;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   R* xi = reinterpret_cast<R*>(smem);
   R* wq = xi + Q;
@@ -234,11 +238,21 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   }
 }
 
+template <class R, int NC, bool EPSQ, int QC, int TC>
+cudaError_t launch_mf_shape(fv_ctx ctx, const MfArgs& a, int grid, int wpb, size_t smem) {
+  cudaError_t e = ensure_smem_attr(ctx, (const void*)contract_mfree<R, NC, EPSQ, QC, TC>, smem);
+  if (e == cudaSuccess) contract_mfree<R, NC, EPSQ, QC, TC><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
+  return e;
+}
+// FP32 evaluations of the common orders use compile-time instantiations.
 template <class R, int NC, bool EPSQ>
 cudaError_t launch_mf(fv_ctx ctx, const MfArgs& a, int grid, int wpb, size_t smem) {
-  cudaError_t e = ensure_smem_attr(ctx, (const void*)contract_mfree<R, NC, EPSQ>, smem);
-  if (e == cudaSuccess) contract_mfree<R, NC, EPSQ><<<grid, 32 * wpb, smem, ctx->stream>>>(a);
-  return e;
+  if constexpr (std::is_same<R, float>::value) {
+    if (a.Q == 10 && a.T == 8) return launch_mf_shape<R, NC, EPSQ, 10, 8>(ctx, a, grid, wpb, smem);
+    if (a.Q == 8 && a.T == 6) return launch_mf_shape<R, NC, EPSQ, 8, 6>(ctx, a, grid, wpb, smem);
+    if (a.Q == 5 && a.T == 5) return launch_mf_shape<R, NC, EPSQ, 5, 5>(ctx, a, grid, wpb, smem);
+  }
+  return launch_mf_shape<R, NC, EPSQ, 0, 0>(ctx, a, grid, wpb, smem);
 }
 template <class R, bool EPSQ>
 cudaError_t launch_mf_nc(fv_ctx ctx, const MfArgs& a, int nc, int grid, int wpb, size_t smem) {

@@ -280,14 +280,20 @@ def test_argument_errors(api, ctx):
     assert ei.value.code in (N.FV_ERR_UNSUPPORTED, N.FV_ERR_ARG)
 
 
-def test_deterministic(api, ctx):
-    prob = cfg("disc")
-    pb = api.problem_from_inputs(ctx, prob, "fp32")
-    params = torch.tensor(prob.params, dtype=torch.float32, device="cuda")
+@pytest.mark.parametrize("k,precision,g_mode", [("disc", "fp32", None), ("annulus", "fp16", None),
+                                                 ("annulus", "bf16", "matrix_free"), ("regular", "fp16", "regular")])
+def test_deterministic(api, ctx, k, precision, g_mode):
+    """Repeated evaluations are bit-identical: fixed-order sums everywhere, and
+    the forward's dynamically handed-out tiles do not change any output."""
+    prob = _uniform_problem(96, 80, 8, 6, (0.3, 0.0), 0.9) if k == "regular" else cfg(k)
+    storage = "bf16" if precision in ("fp16", "bf16") and g_mode is None else None
+    pb = api.problem_from_inputs(ctx, prob, precision, storage, g_mode=g_mode)
+    params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
     o1, g1 = pb.loss_grad(params)
     o1, g1 = o1.clone(), g1.clone()
-    o2, g2 = pb.loss_grad(params)
-    assert torch.equal(o1, o2) and torch.equal(g1, g2)
+    for _ in range(2):
+        o2, g2 = pb.loss_grad(params)
+        assert torch.equal(o1, o2) and torch.equal(g1, g2)
 
 
 @pytest.mark.parametrize("k", ["disc", "inverse"])
