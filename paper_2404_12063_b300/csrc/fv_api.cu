@@ -415,27 +415,39 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
           : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
   if (rc) return rc;
   const double inv_norm = 1.0 / (opts->norm == FV_NORM_TEST ? mesh->Nt : mesh->n_e);
+  // Boundary and sensor terms read U and write the boundary points' seeds and
+  // two partials, disjoint from the contraction's outputs: on the context's
+  // side stream they run concurrently with it (serially when timing kernels).
+  const bool has_bc = bc && pl.n_bd + pl.n_s > 0;
+  const bool concurrent = has_bc && ctx->side && !ctx->timing;
+  const cudaStream_t bst = concurrent ? ctx->side : ctx->stream;
+  if (concurrent) {
+    FV_CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    FV_CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  }
+  if (has_bc) {
+    cudaEvent_t ta;
+    time_begin(ctx, K_BC, &ta);
+    if (pl.prec == FV_FP64)
+      bc_kernel<double><<<1, 256, 0, bst>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const double*)U,
+                                            (double*)UB, pl.P_mesh, pl.P_tot, bcpart);
+    else
+      bc_kernel<float><<<1, 256, 0, bst>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const float*)U,
+                                           (float*)UB, pl.P_mesh, pl.P_tot, bcpart);
+    time_end(ctx, K_BC, ta);
+    FV_CUDA_TRY(cudaGetLastError());
+    if (concurrent) FV_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->side));
+  } else {
+    FV_CUDA_TRY(cudaMemsetAsync(bcpart, 0, 16, ctx->stream));
+  }
   int ncp = 0;
   rc = launch_contract(ctx, mesh, forcing, pl, U, UB, opts->eps, eps_dev ? eps_dev : opts->eps_dev, opts->bx, opts->by,
                        2.0 * inv_norm, cpart, &ncp, R_out);
+  if (concurrent) FV_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));   // join before any return
   if (rc) return rc;
   if (n_str == 4 && UB && pl.P_tot > pl.P_mesh)       // boundary and sensor points: no eps(x, y) seed
     FV_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(UB) + (3 * pl.P_tot + pl.P_mesh) * rsz, 0,
                                 (pl.P_tot - pl.P_mesh) * rsz, ctx->stream));
-  if (bc && pl.n_bd + pl.n_s > 0) {
-    cudaEvent_t ta;
-    time_begin(ctx, K_BC, &ta);
-    if (pl.prec == FV_FP64)
-      bc_kernel<double><<<1, 256, 0, ctx->stream>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const double*)U,
-                                                   (double*)UB, pl.P_mesh, pl.P_tot, bcpart);
-    else
-      bc_kernel<float><<<1, 256, 0, ctx->stream>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const float*)U,
-                                                  (float*)UB, pl.P_mesh, pl.P_tot, bcpart);
-    time_end(ctx, K_BC, ta);
-    FV_CUDA_TRY(cudaGetLastError());
-  } else {
-    FV_CUDA_TRY(cudaMemsetAsync(bcpart, 0, 16, ctx->stream));
-  }
   if (U_copy) FV_CUDA_TRY(cudaMemcpyAsync(U_copy, U, n_str * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
   if (UB_copy && UB)
     FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, n_str * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -496,7 +508,13 @@ extern "C" int fv_ctx_create(fv_ctx* out, int device, void* stream) {
   c->smem_per_sm = prop.sharedMemPerMultiprocessor;
   cudaError_t e = cudaMalloc(&c->err_dev, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    cudaFree(c->err_dev);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     delete c;
     set_error("fv_ctx_create: %s", cudaGetErrorString(e));
     return FV_ERR_CUDA;
@@ -518,8 +536,12 @@ extern "C" int fv_ctx_destroy(fv_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   cudaFree(ctx->ws.ptr);
   cudaFree(ctx->err_dev);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   delete ctx;
   return FV_OK;
 }

@@ -75,6 +75,8 @@ struct fv_ctx_s {
   size_t smem_per_sm = 228 * 1024;
   fv::Workspace ws;
   int* err_dev = nullptr;           // device error word (bounded waits, degenerate elements)
+  cudaStream_t side = nullptr;      // boundary terms concurrent with the contraction (null: serial)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool timing = false;
   std::vector<fv::TimingRec> recs;
   std::vector<cudaEvent_t> free_events;

@@ -621,3 +621,20 @@ def test_fp16_tighter_than_bf16(api, ctx):
         ref = oracle_eval(prob, params.cpu().double().numpy())
         errs[prec] = rel(grad, ref["grad"])
     assert errs["fp16"] < 0.5 * errs["bf16"], errs
+
+
+# ---------------------------------------------------------------- element sharding (multi-GPU logic)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp16", 1e-5)])
+def test_element_shards_on_one_gpu_sum_to_the_whole(api, ctx, precision, tol):
+    """The multi-GPU decomposition run on one GPU: three contiguous element
+    blocks (boundary terms on the first) evaluated with the CUDA path and
+    summed on the host equal the unsharded evaluation."""
+    from paper_2404_12063_b300 import parallel
+    prob = cfg("disc")
+    make = parallel.cuda_evaluator(precision)
+    out_w, grad_w = make(prob)(prob.params)
+    parts = [make(parallel.shard_problem(prob, r, 3))(prob.params) for r in range(3)]
+    out_s = sum(p[0] for p in parts)
+    grad_s = sum(p[1] for p in parts)
+    assert rel(out_s[:4], out_w[:4]) < tol
+    assert rel(grad_s, grad_w) < tol
