@@ -160,9 +160,11 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 template <class R>
 __global__ void __launch_bounds__(256) bc_kernel(const double* __restrict__ val, int n_bd, int n_s, double tau,
                                                  double gamma, const R* __restrict__ U, R* __restrict__ UB,
-                                                 int64_t P_mesh, int64_t P_tot, double* __restrict__ partial2) {
+                                                 int64_t P_mesh, int64_t P_tot, double* __restrict__ partial2,
+                                                 float* __restrict__ seed_max) {
   __shared__ double red[256];
   R lb = 0, ls = 0;
+  float smx = 0.f;
   const R cb = (R)(2.0 * tau / (n_bd > 0 ? n_bd : 1)), cs = (R)(2.0 * gamma / (n_s > 0 ? n_s : 1));
   const int nd = n_bd + n_s;
   for (int d0 = threadIdx.x; d0 < nd; d0 += 4 * blockDim.x) {
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(256) bc_kernel(const double* __restrict__ val,
       R seed;
       if (d < n_bd) { lb += diff * diff; seed = cb * diff; }
       else { ls += diff * diff; seed = cs * diff; }
+      smx = fmaxf(smx, fabsf((float)seed));
       if (UB) {
         UB[gp] = seed;
         UB[P_tot + gp] = (R)0;
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(256) bc_kernel(const double* __restrict__ val,
       }
     }
   }
+  warp_max_to(seed_max, smx);
   const double a = block_sum256((double)lb, red);
   const double b = block_sum256((double)ls, red);
   if (threadIdx.x == 0) { partial2[0] = a; partial2[1] = b; }
@@ -244,27 +248,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict_
       out[4] = d;
     }
   }
-}
-
-// max |seed| over all points (the FP16 reverse sweep scales its adjoints by
-// a power of two derived from it); non-negative floats order like their bits.
-__global__ void __launch_bounds__(256) seed_absmax_kernel(const float* __restrict__ UB, int64_t n,
-                                                          float* __restrict__ out) {
-  // 16-byte loads, four in flight per thread (UB starts on a 256-byte boundary), then the tail
-  float m = 0.f;
-  const int64_t n4 = n / 4, stride = (int64_t)gridDim.x * blockDim.x;
-  const float4* U4 = reinterpret_cast<const float4*>(UB);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += 4 * stride) {
-    float4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = i + u * stride < n4 ? U4[i + u * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) m = fmaxf(m, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
-  }
-  for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) m = fmaxf(m, fabsf(UB[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
 }
 
 // Adam (Kingma & Ba, bias-corrected) on theta and, when trained, eps.  The
@@ -418,6 +401,12 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   // Boundary and sensor terms read U and write the boundary points' seeds and
   // two partials, disjoint from the contraction's outputs: on the context's
   // side stream they run concurrently with it (serially when timing kernels).
+  // FP16 reverse sweep: the kernels that write seeds (contraction, boundary
+  // terms) raise *smax to max |seed|; the reverse sweep scales by it
+  if (want_grad && pl.prec == FV_FP16) {
+    FV_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(float), ctx->stream));
+    pl.seed_max = smax;
+  }
   const bool has_bc = bc && pl.n_bd + pl.n_s > 0;
   const bool concurrent = has_bc && ctx->side && !ctx->timing;
   const cudaStream_t bst = concurrent ? ctx->side : ctx->stream;
@@ -430,10 +419,10 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
     time_begin(ctx, K_BC, &ta);
     if (pl.prec == FV_FP64)
       bc_kernel<double><<<1, 256, 0, bst>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const double*)U,
-                                            (double*)UB, pl.P_mesh, pl.P_tot, bcpart);
+                                            (double*)UB, pl.P_mesh, pl.P_tot, bcpart, pl.seed_max);
     else
       bc_kernel<float><<<1, 256, 0, bst>>>(bc->val, pl.n_bd, pl.n_s, bc->tau, bc->gamma, (const float*)U,
-                                           (float*)UB, pl.P_mesh, pl.P_tot, bcpart);
+                                           (float*)UB, pl.P_mesh, pl.P_tot, bcpart, pl.seed_max);
     time_end(ctx, K_BC, ta);
     FV_CUDA_TRY(cudaGetLastError());
     if (concurrent) FV_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->side));
@@ -452,14 +441,6 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   if (UB_copy && UB)
     FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, n_str * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
   int ngp = 0;
-  if (want_grad && pl.prec == FV_FP16) {
-    cudaEvent_t ts;
-    time_begin(ctx, K_SEED_SCALE, &ts);
-    FV_CUDA_TRY(cudaMemsetAsync(smax, 0, sizeof(float), ctx->stream));
-    seed_absmax_kernel<<<ctx->n_sm * 4, 256, 0, ctx->stream>>>((const float*)UB, 3 * pl.P_tot, smax);
-    time_end(ctx, K_SEED_SCALE, ts);
-    FV_CUDA_TRY(cudaGetLastError());
-  }
   if (want_grad) {
     rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp, smax)
             : launch_mlp_bwd(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp);

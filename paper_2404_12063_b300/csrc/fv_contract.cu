@@ -89,6 +89,7 @@ struct ContractArgs {
   double* partials;     // [gridDim][2]
   int* err;
   double* R_out;        // optional [n_e][Nt] element residuals
+  float* seed_max;      // optional: raised to max |seed| (FP16 reverse sweep)
 };
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
   const int n1 = (Eg * Nt * H1 + kCThreads - 1) / kCThreads;
   const int n2 = (Eg * nch * H2 + kCThreads - 1) / kCThreads;
   KahanR<R> lsum, dsum;
+  float smx = 0.f;                 // largest |seed| this thread wrote
   for (int it = 0;; ++it) {
     const int grp = blockIdx.x + it * gridDim.x;
     if (grp >= a.n_groups) break;
@@ -441,9 +443,11 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
           const int64_t p = (int64_t)(e0 + k) * Nq + c * VEC;
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
+            const R s1 = eps * sx[v] + bx * sv[v], s2 = eps * sy[v] + by * sv[v];
             UB[p + v] = (R)0;
-            UB[a.P_tot + p + v] = eps * sx[v] + bx * sv[v];
-            UB[2 * a.P_tot + p + v] = eps * sy[v] + by * sv[v];
+            UB[a.P_tot + p + v] = s1;
+            UB[2 * a.P_tot + p + v] = s2;
+            smx = fmaxf(smx, fmaxf(fabsf((float)s1), fabsf((float)s2)));
           }
         }
       }
@@ -452,6 +456,7 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
     if (tid == 0) issue(it + S);
   }
   cp_async_wait0();
+  warp_max_to(a.seed_max, smx);
   // loss partials: per-thread compensated sums, then a fixed-order tree in FP64
   double l = (double)lsum.s - (double)lsum.c, d = (double)dsum.s - (double)dsum.c;
 #pragma unroll
@@ -489,6 +494,7 @@ __global__ void __launch_bounds__(kThreads) contract_direct(ContractArgs a) {
   R* UB = reinterpret_cast<R*>(a.UB);
   const int64_t gstride = a.g_stride_bytes / (int64_t)sizeof(Gt);
   KSum lsum, dsum;
+  float smx = 0.f;
   for (int e = blockIdx.x; e < a.n_e; e += gridDim.x) {
     const Gt* Ge = reinterpret_cast<const Gt*>(a.G) + (size_t)e * gstride;
     const R* ux = U + a.P_tot + (int64_t)e * Nq;
@@ -523,13 +529,16 @@ __global__ void __launch_bounds__(kThreads) contract_direct(ContractArgs a) {
           if (a.n_comp == 3) sv += rb * (R)Ge[(size_t)(2 * Nt + j) * Nq + q];
         }
         const int64_t p = (int64_t)e * Nq + q;
+        const R s1 = (R)eps * sx + (R)a.bx * sv, s2 = (R)eps * sy + (R)a.by * sv;
         UB[p] = (R)0;
-        UB[a.P_tot + p] = (R)eps * sx + (R)a.bx * sv;
-        UB[2 * a.P_tot + p] = (R)eps * sy + (R)a.by * sv;
+        UB[a.P_tot + p] = s1;
+        UB[2 * a.P_tot + p] = s2;
+        smx = fmaxf(smx, fmaxf(fabsf((float)s1), fabsf((float)s2)));
       }
     }
     __syncthreads();
   }
+  warp_max_to(a.seed_max, smx);
   if (lane == 0) {
     s_red[warp * 4 + 0] = lsum.s; s_red[warp * 4 + 1] = lsum.c;
     s_red[warp * 4 + 2] = dsum.s; s_red[warp * 4 + 3] = dsum.c;
@@ -800,7 +809,7 @@ int launch_contract(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& pl, con
   a.eps_h = eps; a.eps_d = eps_dev; a.bx = bx; a.by = by; a.rscale = rscale;
   a.elems_per_stage = P.E; a.n_stages = P.S; a.n_groups = P.staged ? (m->n_e + P.E - 1) / P.E : m->n_e;
   a.sh1 = P.sh1; a.sh2 = P.sh2; a.nq_pad = P.nqp;
-  a.partials = partials; a.err = ctx->err_dev; a.R_out = R_out;
+  a.partials = partials; a.err = ctx->err_dev; a.R_out = R_out; a.seed_max = pl.seed_max;
   *n_part = P.grid;
   cudaEvent_t ta;
   time_begin(ctx, K_CONTRACT, &ta);

@@ -223,7 +223,21 @@ struct EvalPlan {
   int n_bd = 0, n_s = 0;
   int64_t P_tot = 0;        // P_mesh + n_bd + n_s
   bool want_grad = false;
+  float* seed_max = nullptr;  // FP16 reverse sweep: the kernels that write seeds raise this to max |seed|
 };
+
+// max(*word, v) for non-negative floats (their bit patterns order like the values)
+__device__ __forceinline__ void atomic_max_nonneg(float* word, float v) {
+  if (v > 0.f) atomicMax(reinterpret_cast<int*>(word), __float_as_int(v));
+}
+
+// A warp's largest value, then one atomic per warp (null word: nothing).
+__device__ __forceinline__ void warp_max_to(float* word, float v) {
+  if (!word) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(word, v);
+}
 
 int launch_mlp_fwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
                    void* U);

@@ -48,6 +48,7 @@ struct MfArgs {
   double bx, by, rscale;
   double* partials;         // [gridDim][2]
   double* R_out;            // optional [n_e][T*T]
+  float* seed_max;          // optional: raised to max |seed| (FP16 reverse sweep)
 };
 
 // One element's inputs staged in shared memory: u_x, u_y (and eps(x, y)) at its
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
   R* UB = reinterpret_cast<R*>(a.UB);
   const R* F = reinterpret_cast<const R*>(a.Fr);
   KahanR<R> lsum, dsum;
+  float smx = 0.f;                 // largest |seed| this thread wrote
 
   // the element's u_x, u_y and F rows go to a stage with cp.async, one element ahead
   auto fetch = [&](int e, R* st) {
@@ -205,15 +207,18 @@ __global__ void __launch_bounds__(256) contract_mfree(MfArgs a) {
         const R gy = w * (x_xi * seta - x_eta * sxi);          // sum_j Rbar_j Gy[j][q]
         const R gv = NC == 3 ? w * (x_xi * y_eta - x_eta * y_xi) * sv : (R)0;
         const R eq = EPSQ ? st[2 * Nq + Nt + q] : eps;
+        const R s1 = eq * gx + bx * gv, s2 = eq * gy + by * gv;
         UB[p0 + q] = (R)0;
-        UB[a.P_tot + p0 + q] = eq * gx + bx * gv;
-        UB[2 * a.P_tot + p0 + q] = eq * gy + by * gv;
+        UB[a.P_tot + p0 + q] = s1;
+        UB[2 * a.P_tot + p0 + q] = s2;
+        smx = fmaxf(smx, fmaxf(fabsf((float)s1), fabsf((float)s2)));
         if (EPSQ) UB[3 * a.P_tot + p0 + q] = st[q] * gx + st[Nq + q] * gy;
       }
     }
     __syncwarp();
   }
   cp_async_wait0();
+  warp_max_to(a.seed_max, smx);
   // loss partials: per-thread compensated sums, a fixed-order tree in FP64 per warp, warps in order
   __shared__ double s_red[8][2];
   double l = (double)lsum.s - (double)lsum.c, d = (double)dsum.s - (double)dsum.c;
@@ -304,7 +309,7 @@ int launch_contract_mfree(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan& p
   a.Fr = pl.prec == FV_FP64 ? (const void*)f->F : (const void*)f->F32;
   a.U = U; a.UB = UB; a.P_tot = pl.P_tot;
   a.eps_h = eps; a.eps_d = eps_dev; a.bx = bx; a.by = by; a.rscale = rscale;
-  a.partials = partials; a.R_out = R_out;
+  a.partials = partials; a.R_out = R_out; a.seed_max = pl.seed_max;
   *n_part = grid;
   cudaEvent_t ta;
   time_begin(ctx, K_CONTRACT, &ta);

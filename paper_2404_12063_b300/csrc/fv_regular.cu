@@ -60,6 +60,7 @@ struct RegArgs {
   double* partials;       // [gridDim][2]
   double* R_out;          // optional [n_e][T*T]
   int* err;
+  float* seed_max;        // optional: raised to max |seed| (FP16 reverse sweep)
 };
 
 bool make_reg_plan(int Q, int T, int nc, RegPlan* p) {
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
   uint32_t phase = 0;
   bool failed = false;
   double lsum = 0.0, dsum = 0.0;
+  float smx = 0.f;                 // largest |seed| this thread wrote
   // TMEM lane quarter q4 of this warp and its half of the tile's elements (columns);
   // GEMM row of this thread: M = 128 -> row = lane 32 q4 + l; M = 64 -> row 16 q4 + l (l < 16)
   const int q4 = warp & 3, c_lo = (warp >> 2) * (kRegTile / 2), c_hi = c_lo + kRegTile / 2;
@@ -329,9 +331,11 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
           const float jx = sJ[n * 3], jy = sJ[n * 3 + 1], jj = sJ[n * 3 + 2];
           const float sx = dx[i] * inv, sy = dy[i] * inv, sv = NC == 3 ? dvv[i] * inv : 0.f;
           const int64_t p = (int64_t)e * Nq + row2;
+          const float s1 = eps * jx * sx + bx * jj * sv, s2 = eps * jy * sy + by * jj * sv;
           a.UB[p] = 0.f;
-          a.UB[a.P_tot + p] = eps * jx * sx + bx * jj * sv;
-          a.UB[2 * a.P_tot + p] = eps * jy * sy + by * jj * sv;
+          a.UB[a.P_tot + p] = s1;
+          a.UB[2 * a.P_tot + p] = s2;
+          smx = fmaxf(smx, fmaxf(fabsf(s1), fabsf(s2)));
         }
       }
     }
@@ -340,6 +344,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) contract_regular_tc(RegArgs a)
     tc_fence_before();
     __syncthreads();
   }
+  warp_max_to(a.seed_max, smx);
   // loss and eps-derivative partials: per-thread sums, a fixed-order warp tree, warps in order
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -466,7 +471,7 @@ int launch_contract_regular(fv_ctx ctx, fv_mesh m, fv_forcing f, const EvalPlan&
   a.F = f->F32;
   a.U = static_cast<const float*>(U); a.UB = static_cast<float*>(UB); a.P_tot = pl.P_tot;
   a.eps_h = eps; a.eps_d = eps_dev; a.bx = bx; a.by = by; a.rscale = rscale;
-  a.partials = partials; a.R_out = R_out; a.err = ctx->err_dev;
+  a.partials = partials; a.R_out = R_out; a.err = ctx->err_dev; a.seed_max = pl.seed_max;
   const int grid = regular_grid(ctx, m);
   *n_part = grid;
   cudaEvent_t ta;
