@@ -62,13 +62,39 @@ KERNEL_SOURCES = {"contract": "fv_contract.cu", "mlp_bwd_tc": "fv_mlp_tc.cu", "m
                   "mlp_bwd": "fv_mlp_simt.cu", "mlp_fwd": "fv_mlp_simt.cu"}
 
 
+def strip_comments(src):
+    """C/C++ source without its comments and blank space, so that an edit of
+    comments alone keeps the hash of the code that is compiled."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_sha(kernel):
+    """Hash of the kernel's source file with comments and blank space removed."""
     import hashlib
     path = os.path.join(ROOT, "paper_2404_12063_b300", "csrc", KERNEL_SOURCES.get(kernel, ""))
     try:
-        return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+        code = strip_comments(open(path, encoding="utf-8").read())
     except OSError:
         return None
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel, variant):

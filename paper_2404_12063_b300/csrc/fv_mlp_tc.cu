@@ -174,9 +174,7 @@ __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_sm
   }
 }
 
-// MMAs into one accumulator run as a dependent chain; MMAs into independent
-// accumulators overlap in the tensor pipe.  So the three streams' MMAs are
-// issued round-robin (K step outer, stream inner).
+// The three streams' MMAs are issued round-robin (K step outer, stream inner).
 
 // Forward MMAs of map i: D_s (columns s*HP) = H_{i-1,s} W_i^T, K = Kin, N = Nout.
 __device__ __forceinline__ void issue_fwd(uint32_t fmt, uint32_t tD, uint32_t abuf, uint32_t wbuf, int Kin, int Nout,

@@ -55,3 +55,24 @@ def test_no_gpu_gives_an_error_code(lib):
     h = C.c_void_p()
     rc = lib.fv_ctx_create(C.byref(h), 0, None)
     assert rc in (N.FV_ERR_CUDA, N.FV_ERR_ARG)
+
+
+def test_traffic_record_survives_comment_edits_only():
+    """The bench reports an ncu traffic figure only while the kernel's code is
+    the one that was captured; comments and blank space do not count."""
+    import importlib.util
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_host", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        spec.loader.exec_module(bench)
+    finally:
+        sys.argv = argv
+    a = 'asm volatile("mov.u32 %0, 1; // x" : "=r"(v)); // note\nint  y;\n/* block */ z'
+    b = 'asm volatile("mov.u32 %0, 1; // x" : "=r"(v));\nint y; z'
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments(a) != bench.strip_comments(a.replace("int", "long"))
+    assert bench.strip_comments("char c = '\"'; // q") == "char c = '\"';"
