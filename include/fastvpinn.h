@@ -109,6 +109,18 @@ const char* fv_last_error(void);
  * synchronises the stream and returns accumulated milliseconds and launch
  * counts per kernel kind (names: fv_kernel_name).  Off by default. */
 int fv_ctx_enable_timing(fv_ctx ctx, int on);
+
+/* Activation stash of the tensor-core reverse sweep (FV_BF16 / FV_FP16
+ * gradients of networks with 3 or 4 hidden layers), on by default: the
+ * forward kernel also writes, per 128-point tile, the hidden activations of
+ * the layers below the last hidden map (value and both tangents, 16-bit, 768
+ * bytes per point and layer at width 50) to the context's workspace, and the
+ * reverse kernel reads them by bulk copies instead of recomputing those maps
+ * (Sec. 4.4's tensor form of the loss; the reverse sweep of the network in
+ * Eq. NN).  Off: the reverse kernel recomputes them.  Results are bitwise the
+ * same either way.  A fixed scratch area too small for it (fv_loss_grad_noalloc)
+ * falls back to recomputing.  Errors: FV_ERR_ARG (null context). */
+int fv_ctx_set_activation_stash(fv_ctx ctx, int on);
 int fv_ctx_kernel_times(fv_ctx ctx, int max_kinds, double* ms, int64_t* launches, int* n_kinds);
 const char* fv_kernel_name(int kind);
 int fv_ctx_reset_kernel_times(fv_ctx ctx);

@@ -52,6 +52,7 @@ SIGNATURES = {
     "fv_ctx_destroy": [_vp],
     "fv_last_error": [],
     "fv_ctx_enable_timing": [_vp, C.c_int],
+    "fv_ctx_set_activation_stash": [_vp, C.c_int],
     "fv_ctx_kernel_times": [_vp, C.c_int, C.POINTER(C.c_double), _i64p, C.POINTER(C.c_int)],
     "fv_kernel_name": [C.c_int],
     "fv_ctx_reset_kernel_times": [_vp],

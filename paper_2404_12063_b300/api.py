@@ -48,6 +48,11 @@ class Context:
     def enable_timing(self, on: bool = True):
         N.call("fv_ctx_enable_timing", self.h, int(on))
 
+    def set_activation_stash(self, on: bool = True):
+        """Tensor-core reverse sweep: read the forward's stored hidden
+        activations (on, the default) or recompute them (off); bitwise equal."""
+        N.call("fv_ctx_set_activation_stash", self.h, int(on))
+
     def kernel_times(self) -> dict:
         ms = (C.c_double * 32)()
         ln = (C.c_int64 * 32)()

@@ -314,7 +314,7 @@ int check_eval(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_
 }
 
 struct WsLayout {
-  size_t U, UB, cpart, bcpart, gpart, smax, ctr, total;
+  size_t U, UB, cpart, bcpart, gpart, smax, ctr, stash, total;
 };
 
 // The core evaluation shared by fv_loss, fv_loss_grad and fv_inverse_step.
@@ -368,6 +368,11 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
   w.smax = o; o += al(16);
   w.ctr = o; o += al(16);
+  // activation stash of the tensor-core reverse sweep; left out (the reverse
+  // kernel recomputes) when a fixed scratch area has no room for it
+  size_t stash_bytes = tc && want_grad && ctx->tc_stash ? mlp_tc_stash_bytes(pl) : 0;
+  if (fixed_ws && o + al(stash_bytes) > fixed_ws_bytes) stash_bytes = 0;
+  w.stash = o; o += al(stash_bytes);
   w.total = o;
   if (ws_bytes_only) {          // size query only: nothing is launched
     *ws_bytes_only = w.total;
@@ -392,9 +397,10 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   double* gpart = reinterpret_cast<double*>(b + w.gpart);
   float* smax = reinterpret_cast<float*>(b + w.smax);
   int* tile_ctr = reinterpret_cast<int*>(b + w.ctr);
+  void* stash = stash_bytes ? b + w.stash : nullptr;
   const double* Xe = bc ? bc->xy : nullptr;
 
-  rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U, tile_ctr)
+  rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U, tile_ctr, stash)
           : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
   if (rc) return rc;
   const double inv_norm = 1.0 / (opts->norm == FV_NORM_TEST ? mesh->Nt : mesh->n_e);
@@ -442,7 +448,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
     FV_CUDA_TRY(cudaMemcpyAsync(UB_copy, UB, n_str * pl.P_tot * rsz, cudaMemcpyDeviceToDevice, ctx->stream));
   int ngp = 0;
   if (want_grad) {
-    rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp, smax)
+    rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp, smax, stash)
             : launch_mlp_bwd(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp);
     if (rc) return rc;
   }
@@ -524,6 +530,13 @@ extern "C" int fv_ctx_destroy(fv_ctx ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   delete ctx;
+  return FV_OK;
+}
+
+extern "C" int fv_ctx_set_activation_stash(fv_ctx ctx, int on) {
+  clear_error();
+  FV_CHECK_ARG(ctx, "fv_ctx_set_activation_stash: null context");
+  ctx->tc_stash = on != 0;
   return FV_OK;
 }
 
@@ -794,6 +807,7 @@ extern "C" int fv_step_graph_create(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing
   cap_ctx.n_sm = ctx->n_sm;
   cap_ctx.smem_optin = ctx->smem_optin;
   cap_ctx.smem_per_sm = ctx->smem_per_sm;
+  cap_ctx.tc_stash = ctx->tc_stash;
   cap_ctx.err_dev = ctx->err_dev;
   fv_mesh_s mesh_copy = *mesh;
   mesh_copy.ctx = &cap_ctx;
@@ -922,6 +936,7 @@ int batch_capture(fv_batch b, int S) {
     lane_ctx.tc_ctas_cap = S > 1 ? 1 : ctx->tc_ctas_cap;   // leave SM room for the other streams' kernels
     lane_ctx.smem_optin = ctx->smem_optin;
     lane_ctx.smem_per_sm = ctx->smem_per_sm;
+    lane_ctx.tc_stash = ctx->tc_stash;
     lane_ctx.err_dev = ctx->err_dev;
     const fv_instance& in = b->inst[i];
     // the handles were created on ctx; evaluate them on the lane context

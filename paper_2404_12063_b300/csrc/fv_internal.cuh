@@ -71,6 +71,7 @@ struct fv_ctx_s {
   cudaStream_t stream = nullptr;
   int n_sm = 148;
   int tc_ctas_cap = 0;              // > 0: at most this many tensor-core MLP CTAs per SM (kernels sharing the GPU)
+  bool tc_stash = true;             // tensor-core reverse sweep reads stored activations (false: recomputes them)
   size_t smem_optin = 227 * 1024;
   size_t smem_per_sm = 228 * 1024;
   fv::Workspace ws;
@@ -267,12 +268,15 @@ int launch_finalize(fv_ctx ctx, const EvalPlan& pl, const double* cpart, int n_c
                     void* grad, double* out);
 
 // Tensor-core MLP paths (tcgen05).
+// stash: null, or mlp_tc_stash_bytes(pl) bytes that the forward fills with the
+// hidden activations the reverse sweep reads instead of recomputing them.
 int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
                       const double* Xextra, void* U,
-                      int* tile_counter);
+                      int* tile_counter, void* stash);
 int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh,
                       const double* Xextra, const void* UB, double* gpart, int* n_blocks_out,
-                      const float* seed_absmax);
+                      const float* seed_absmax, const void* stash);
+size_t mlp_tc_stash_bytes(const EvalPlan& pl);   // 0: this network has no stash
 bool tc_supported(const EvalPlan& pl);
 int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl);
 

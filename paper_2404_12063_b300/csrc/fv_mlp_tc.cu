@@ -50,10 +50,16 @@ struct TcPlan {
   int o_z;                  // adjoint tile (reverse kernel)
   int o_x;                  // layer-0 input tile (reverse kernel): 3 streams x 128 x 16
   int o_red;                // FP32 scratch [128][4] (output-layer partial sums)
-  int o_bar;                // mbarrier (8 B) + TMEM base (4 B) + flags (4 B) + two upcoming tile indices (8 B)
+  int o_bar;                // MMA mbarrier (8 B) + TMEM base (4 B) + flags (4 B) + two upcoming tile indices
+                            // (8 B, forward) or the activation-load mbarrier (8 B, reverse)
   int smem;
   int tmem_cols;
   int c_wbar[kMaxLayers];   // TMEM column of the weight-gradient accumulator of map i (reverse)
+  // Activation stash (networks of 3 or 4 hidden layers): H_j for j = stash_lo ..
+  // L-3, the stored layers below the last hidden map, written per tile by the
+  // forward kernel and read by the reverse kernel instead of recomputing maps
+  // 1 .. L-3; slot_bytes per tile and layer (3 streams x 128 rows x HP columns).
+  int n_stash, stash_lo, slot_bytes;
 };
 
 struct TcArgs {
@@ -68,6 +74,7 @@ struct TcArgs {
   double* gpart;            // [grid][n_params] (reverse)
   const float* seed_absmax; // device max |seed| (FP16 reverse sweep) or null
   int* tile_ctr;            // forward: tiles handed out beyond the first one per CTA (zero at launch)
+  uint8_t* stash;           // [n_tiles][n_stash][slot_bytes] activation tiles, or null (recompute)
   int* err;
 };
 
@@ -298,6 +305,10 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
         tc_fence_after();
         const bool last = i == L - 2;
         const int wo = pl.w[i + 1];
+        // H_i also goes to the stash (same tile layout) when the reverse sweep reads it
+        uint8_t* gst = nullptr;
+        if (a.stash && i >= pl.stash_lo && i < pl.stash_lo + pl.n_stash)
+          gst = a.stash + (tile * pl.n_stash + (i - pl.stash_lo)) * (int64_t)pl.slot_bytes;
         if (c0 < Nout) {
 #pragma unroll
           for (int sc = 0; sc < 16; sc += 8) {
@@ -333,6 +344,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
               st8(buf, Nout, p, cc, pv);
               st8(buf + 256 * Nout, Nout, p, cc, px);
               st8(buf + 512 * Nout, Nout, p, cc, py);
+              if (gst) {
+                const uint64_t pol = l2_evict_first();
+                st8_global(gst, Nout, p, cc, pv, pol);
+                st8_global(gst + 256 * Nout, Nout, p, cc, px, pol);
+                st8_global(gst + 512 * Nout, Nout, p, cc, py, pol);
+              }
             }
           }
         }
@@ -384,9 +401,15 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   const float* s_small = reinterpret_cast<const float*>(sm + pl.o_small);
   uint8_t* xbuf = sm + pl.o_x;
   uint8_t* zb = sm + pl.o_z;
+  // activation stash: the tile's stored layers arrive by bulk copies on ldbar
+  // (one arrival per layer); the next tile's are requested as soon as their
+  // buffers are dead in this tile
+  uint64_t* ldbar = reinterpret_cast<uint64_t*>(sm + pl.o_bar + 24);
+#define FV_STASH (a.stash != nullptr && pl.n_stash > 0)
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
     mbar_init(bar, 1);
+    if (FV_STASH) mbar_init(ldbar, pl.n_stash);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_load_weights<OP>(pl, a.params, sm);
@@ -422,6 +445,16 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); return false; }
     tc_fence_after();
     return true;
+  };
+  // tid 0: request stash layers j of tile t whose buffer (j & 1) is in `bufs`
+  auto stash_request = [&](int64_t t, int bufs) {
+    for (int j = pl.stash_lo; j < pl.stash_lo + pl.n_stash; ++j) {
+      if (!((bufs >> (j & 1)) & 1)) continue;
+      const uint32_t bytes = 3u * 256u * (uint32_t)pl.WP[j];
+      mbar_expect_tx(ldbar, bytes);
+      bulk_load(sm + pl.o_buf[j & 1], a.stash + (t * pl.n_stash + (j - pl.stash_lo)) * (int64_t)pl.slot_bytes, bytes,
+                ldbar, l2_evict_first());
+    }
   };
   auto publish = [&]() {            // make this thread's shared stores visible to the tensor core
     fence_proxy_async();
@@ -490,6 +523,13 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   PointIn nxt;
   if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   bool h0_ready = false;           // H_0 of this tile already in buf[0] (computed under the previous tile's MMAs)
+  // with the stash, buf[0] takes a stashed layer (4 hidden layers) or H_0 (3)
+#define FV_STASH_BUF0 (FV_STASH && pl.n_stash == 2)
+  uint32_t ldstate = 0;            // bit 0: ldbar phase to wait for; bit 1: copies requested, not waited for
+  if (FV_STASH && blockIdx.x < n_tiles) {
+    if (tid == 0) stash_request(blockIdx.x, 3);
+    ldstate |= 2u;
+  }
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     const float x = (float)nxt.x, y = (float)nxt.y;
     const float su = sc * nxt.s[0], sx = sc * nxt.s[1], sy = sc * nxt.s[2];
@@ -504,7 +544,16 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     // ---- forward recompute; the last hidden map's epilogue applies the output
     //      layer and the seeds and writes Zbar_{L-2} (its H is never stored)
     const int last = L - 2;
-    if (last >= 1) {
+    if (FV_STASH) {
+      // stored layers from the forward kernel; maps 1 .. last-1 are not recomputed
+      if (!FV_STASH_BUF0 && !h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+      const bool ok = mbar_wait(ldbar, ldstate & 1u);
+      ldstate = (ldstate & 1u) ^ 1u;
+      if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); failed = true; break; }
+      publish();
+      issue_fwd_map(last);
+      if (!sync_mma()) { failed = true; break; }
+    } else if (last >= 1) {
       if (!h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
       publish();
       for (int i = 1; i < last; ++i) {
@@ -596,7 +645,14 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
           issue_wbar0(OP::fmt, tD + pl.c_wbar[0], su32(zb), pl.WP[0], bsrc, (wfirst >> 0) & 1u);
         wfirst &= ~(1u << i);
         mma_commit(bar);
+        // the next tile's stashed layers into buffers this tile no longer reads:
+        // buf[1] from step 1 on (only H_0 in buf[0] is left), buf[0] at step 0
+        if (FV_STASH && has_next && i <= 1) {
+          fence_proxy_async();
+          stash_request(tile + gridDim.x, i == 1 ? 2 : 1);
+        }
       }
+      if (FV_STASH && has_next && i <= 1) ldstate |= 2u;
       // CUDA-core work on dead tiles while the tensor core runs: H_0 for map 1's
       // reverse step into buf[0] (H_2 there is dead once map 3's step is done),
       // and under map 0's step the next tile's H_0 (buf[0] held this tile's H_0,
@@ -606,7 +662,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         bufH[0] = 0;
       }
       if (i == 0) {
-        h0_ready = last >= 1 && has_next;
+        h0_ready = last >= 1 && has_next && !FV_STASH_BUF0;
         if (h0_ready) layer0_store<OP>(pl, s_small, (float)nxt.x, (float)nxt.y, p, c0, sm + pl.o_buf[0]);
       }
       if (!sync_mma()) { failed = true; break; }
@@ -653,6 +709,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       }
     }
   }
+  if (ldstate & 2u) mbar_wait(ldbar, ldstate & 1u);   // after a failure: let requested copies land
+#undef FV_STASH_BUF0
+#undef FV_STASH
   // ---- write this CTA's gradient partials
   uint32_t* s_flags = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 12);
   if (tid == 0) *s_flags = wfirst;          // accumulators never written by this CTA
@@ -756,6 +815,10 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
   while (t < cols) t *= 2;
   if (t > 512) return false;
   p->tmem_cols = t;
+  const int last = s.L - 2;
+  p->stash_lo = std::max(1, last - 2);
+  p->n_stash = (last == 2 || last == 3) ? last - p->stash_lo : 0;
+  p->slot_bytes = 3 * kTile * HP * 2;
   return true;
 }
 
@@ -812,14 +875,22 @@ int mlp_bwd_tc_blocks(fv_ctx ctx, const EvalPlan& pl) {
   return tc_grid(ctx, p, true, pl.prec == FV_FP16, pl.P_tot);
 }
 
+size_t mlp_tc_stash_bytes(const EvalPlan& pl) {
+  TcPlan p;
+  if (!make_tc_plan(pl, true, &p) || p.n_stash == 0) return 0;
+  const int64_t n_tiles = (pl.P_tot + kTile - 1) / kTile;
+  return (size_t)n_tiles * p.n_stash * p.slot_bytes;
+}
+
 int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xm, const double* Xe,
-                      void* U, int* tile_counter) {
+                      void* U, int* tile_counter, void* stash) {
   TcArgs a;
   if (!make_tc_plan(pl, false, &a.pl)) { set_error("tensor-core path: unsupported network"); return FV_ERR_UNSUPPORTED; }
   a.params = static_cast<const float*>(params);
   a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot;
   a.U = static_cast<float*>(U); a.UB = nullptr; a.gpart = nullptr; a.seed_absmax = nullptr; a.err = ctx->err_dev;
   a.tile_ctr = tile_counter;
+  a.stash = static_cast<uint8_t*>(stash);
   const int grid = tc_grid(ctx, a.pl, false, pl.prec == FV_FP16, pl.P_tot);
   cudaError_t e = cudaMemsetAsync(tile_counter, 0, sizeof(int), ctx->stream);
   if (e != cudaSuccess) {
@@ -834,7 +905,7 @@ int launch_mlp_fwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const 
 }
 
 int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xm, const double* Xe,
-                      const void* UB, double* gpart, int* nb, const float* seed_absmax) {
+                      const void* UB, double* gpart, int* nb, const float* seed_absmax, const void* stash) {
   TcArgs a;
   if (!make_tc_plan(pl, true, &a.pl)) { set_error("tensor-core path: unsupported network"); return FV_ERR_UNSUPPORTED; }
   a.params = static_cast<const float*>(params);
@@ -842,6 +913,7 @@ int launch_mlp_bwd_tc(fv_ctx ctx, const EvalPlan& pl, const void* params, const 
   a.U = nullptr; a.UB = static_cast<const float*>(UB); a.gpart = gpart; a.err = ctx->err_dev;
   a.seed_absmax = pl.prec == FV_FP16 ? seed_absmax : nullptr;
   a.tile_ctr = nullptr;
+  a.stash = static_cast<uint8_t*>(const_cast<void*>(stash));
   const int grid = mlp_bwd_tc_blocks(ctx, pl);
   *nb = grid;
   cudaEvent_t ta;

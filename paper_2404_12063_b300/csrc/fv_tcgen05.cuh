@@ -1,8 +1,8 @@
 // tcgen05 building blocks shared by the tensor-core kernels (hand-written
 // PTX for sm_103a): tensor-memory allocation, 16-bit MMAs with FP32
 // accumulators in tensor memory, commit to an mbarrier, bounded waits, TMEM
-// loads, shared-memory matrix descriptors (no swizzle) and the core-matrix
-// tile layout (8 rows x 16 bytes).
+// loads, bulk copies, shared-memory matrix descriptors (no swizzle) and the
+// core-matrix tile layout (8 rows x 16 bytes).
 #pragma once
 
 #include <cstdint>
@@ -67,6 +67,24 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Bulk copies (cp.async.bulk) from global to shared memory: addresses 16-byte
+// aligned, sizes multiples of 16; they complete on an mbarrier armed with the
+// bytes to expect.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+// L2 policy for data streamed through once (first to be evicted).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+               ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(bar)), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -128,6 +146,12 @@ __device__ __forceinline__ uint32_t row_off(int p, int Kb) { return (p >> 3) * (
 // 8 columns [c, c+8) of row p (one 16-byte core-matrix row segment).
 __device__ __forceinline__ void st8(uint8_t* stream, int Kb, int p, int c, const uint32_t pk[4]) {
   *reinterpret_cast<uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+// The same 16 bytes to global memory at the tile's layout offset, with an L2 policy.
+__device__ __forceinline__ void st8_global(uint8_t* stream, int Kb, int p, int c, const uint32_t pk[4], uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(stream + row_off(p, Kb) + (c >> 3) * 128),
+               "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3]), "l"(pol)
+               : "memory");
 }
 template <class OP>
 __device__ __forceinline__ void ld8(const uint8_t* stream, int Kb, int p, int c, float v[8]) {

@@ -599,7 +599,7 @@ def test_tensor_core_intermediates_elementwise(api, ctx, precision):
     assert rel(R, ref["R"]) < 2e-2
 
 
-@pytest.mark.parametrize("widths", [[2, 20, 1], [2, 24, 16, 1], [2, 40, 40, 40, 40, 40, 1]])
+@pytest.mark.parametrize("widths", [[2, 20, 1], [2, 24, 16, 1], [2, 30, 30, 30, 1], [2, 40, 40, 40, 40, 40, 1]])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_network_depths(api, ctx, widths, precision):
     prob = _with(cfg("disc"), widths=widths, params=fi.random_bias_params(widths, 5, 1))
@@ -610,6 +610,29 @@ def test_tensor_core_network_depths(api, ctx, widths, precision):
 def test_tensor_core_convection_and_eps(api, ctx, precision):
     prob = _with(fi.inverse_cd2d(32), eps=0.7)
     check_against_oracle(api, ctx, prob, precision, tol_lv=6e-2 if precision == "bf16" else None)
+
+
+@pytest.mark.parametrize("widths", [None, [2, 30, 30, 30, 1]])
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_activation_stash_equals_recompute(api, ctx, widths, precision):
+    """The reverse sweep that reads the forward's stored activations (4 or 3
+    hidden layers) returns bitwise what recomputing them gives.  The annulus
+    has 6,400 tiles of 128 points, so every CTA also requests its next tile's
+    layers under its current tile's last reverse steps."""
+    prob = cfg("annulus")
+    if widths is not None:
+        prob = _with(prob, widths=widths, params=fi.random_bias_params(widths, 5, 1))
+    pb = api.problem_from_inputs(ctx, prob, precision, "bf16")
+    params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+    try:
+        ctx.set_activation_stash(True)
+        o1, g1 = pb.loss_grad(params)
+        o1, g1 = o1.clone(), g1.clone()
+        ctx.set_activation_stash(False)
+        o2, g2 = pb.loss_grad(params)
+    finally:
+        ctx.set_activation_stash(True)
+    assert torch.equal(o1, o2) and torch.equal(g1, g2)
 
 
 def test_fp16_tighter_than_bf16(api, ctx):
