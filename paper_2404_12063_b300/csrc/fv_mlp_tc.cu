@@ -305,10 +305,15 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
         tc_fence_after();
         const bool last = i == L - 2;
         const int wo = pl.w[i + 1];
-        // H_i also goes to the stash (same tile layout) when the reverse sweep reads it
+        // H_i also goes to the stash (same tile layout) when the reverse sweep
+        // reads it: this thread's row and first column chunk of the value stream
         uint8_t* gst = nullptr;
-        if (a.stash && i >= pl.stash_lo && i < pl.stash_lo + pl.n_stash)
-          gst = a.stash + (tile * pl.n_stash + (i - pl.stash_lo)) * (int64_t)pl.slot_bytes;
+        uint64_t pol = 0;
+        if (a.stash && i >= pl.stash_lo && i < pl.stash_lo + pl.n_stash && c0 < Nout) {
+          gst = a.stash + (tile * pl.n_stash + (i - pl.stash_lo)) * (int64_t)pl.slot_bytes + row_off(p, Nout) +
+                (c0 >> 3) * 128;
+          pol = l2_evict_first();
+        }
         if (c0 < Nout) {
 #pragma unroll
           for (int sc = 0; sc < 16; sc += 8) {
@@ -345,10 +350,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
               st8(buf + 256 * Nout, Nout, p, cc, px);
               st8(buf + 512 * Nout, Nout, p, cc, py);
               if (gst) {
-                const uint64_t pol = l2_evict_first();
-                st8_global(gst, Nout, p, cc, pv, pol);
-                st8_global(gst + 256 * Nout, Nout, p, cc, px, pol);
-                st8_global(gst + 512 * Nout, Nout, p, cc, py, pol);
+                st16_global(gst + sc * 16, pv, pol);
+                st16_global(gst + 256 * Nout + sc * 16, px, pol);
+                st16_global(gst + 512 * Nout + sc * 16, py, pol);
               }
             }
           }
