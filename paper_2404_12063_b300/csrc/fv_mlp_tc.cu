@@ -305,15 +305,13 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
         tc_fence_after();
         const bool last = i == L - 2;
         const int wo = pl.w[i + 1];
-        // H_i also goes to the stash (same tile layout) when the reverse sweep
-        // reads it: this thread's row and first column chunk of the value stream
+        // H_i also goes to the stash (same tile layout, streaming stores) when the
+        // reverse sweep reads it: this thread's row and first column chunk of the
+        // value stream
         uint8_t* gst = nullptr;
-        uint64_t pol = 0;
-        if (a.stash && i >= pl.stash_lo && i < pl.stash_lo + pl.n_stash && c0 < Nout) {
+        if (a.stash && i >= pl.stash_lo && i < pl.stash_lo + pl.n_stash && c0 < Nout)
           gst = a.stash + (tile * pl.n_stash + (i - pl.stash_lo)) * (int64_t)pl.slot_bytes + row_off(p, Nout) +
                 (c0 >> 3) * 128;
-          pol = l2_evict_first();
-        }
         if (c0 < Nout) {
 #pragma unroll
           for (int sc = 0; sc < 16; sc += 8) {
@@ -350,9 +348,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
               st8(buf + 256 * Nout, Nout, p, cc, px);
               st8(buf + 512 * Nout, Nout, p, cc, py);
               if (gst) {
-                st16_global(gst + sc * 16, pv, pol);
-                st16_global(gst + 256 * Nout + sc * 16, px, pol);
-                st16_global(gst + 512 * Nout + sc * 16, py, pol);
+                __stcs(reinterpret_cast<uint4*>(gst + sc * 16), make_uint4(pv[0], pv[1], pv[2], pv[3]));
+                __stcs(reinterpret_cast<uint4*>(gst + 256 * Nout + sc * 16), make_uint4(px[0], px[1], px[2], px[3]));
+                __stcs(reinterpret_cast<uint4*>(gst + 512 * Nout + sc * 16), make_uint4(py[0], py[1], py[2], py[3]));
               }
             }
           }

@@ -147,12 +147,6 @@ __device__ __forceinline__ uint32_t row_off(int p, int Kb) { return (p >> 3) * (
 __device__ __forceinline__ void st8(uint8_t* stream, int Kb, int p, int c, const uint32_t pk[4]) {
   *reinterpret_cast<uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
-// 16 bytes to global memory with an L2 policy.
-__device__ __forceinline__ void st16_global(uint8_t* dst, const uint32_t pk[4], uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "r"(pk[0]), "r"(pk[1]),
-               "r"(pk[2]), "r"(pk[3]), "l"(pol)
-               : "memory");
-}
 template <class OP>
 __device__ __forceinline__ void ld8(const uint8_t* stream, int Kb, int p, int c, float v[8]) {
   const uint4 x = *reinterpret_cast<const uint4*>(stream + row_off(p, Kb) + (c >> 3) * 128);
