@@ -44,6 +44,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fv_ctx_create(None, 0, None) == N.FV_ERR_ARG
     assert b"null" in lib.fv_last_error()
     assert lib.fv_mesh_info(None, None) == N.FV_ERR_ARG
+    assert lib.fv_ctx_set_activation_stash(None, 1) == N.FV_ERR_ARG
     assert lib.fv_kernel_name(3) == b"contract"
 
 
