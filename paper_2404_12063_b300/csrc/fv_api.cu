@@ -387,6 +387,12 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
     base = fixed_ws;
   } else {
     rc = ws_reserve(ctx, w.total, &base);
+    if (rc == FV_ERR_OOM && stash_bytes) {   // no room for the stash: the reverse sweep recomputes
+      cudaGetLastError();
+      w.total -= al(stash_bytes);
+      stash_bytes = 0;
+      rc = ws_reserve(ctx, w.total, &base);
+    }
     if (rc) return rc;
   }
   char* b = static_cast<char*>(base);
