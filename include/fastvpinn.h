@@ -119,7 +119,8 @@ int fv_ctx_enable_timing(fv_ctx ctx, int on);
  * (Sec. 4.4's tensor form of the loss; the reverse sweep of the network in
  * Eq. NN).  Off: the reverse kernel recomputes them.  Results are bitwise the
  * same either way.  A fixed scratch area too small for it (fv_loss_grad_noalloc)
- * falls back to recomputing.  Errors: FV_ERR_ARG (null context). */
+ * or a workspace allocation that fails with it falls back to recomputing.
+ * Errors: FV_ERR_ARG (null context). */
 int fv_ctx_set_activation_stash(fv_ctx ctx, int on);
 int fv_ctx_kernel_times(fv_ctx ctx, int max_kinds, double* ms, int64_t* launches, int* n_kinds);
 const char* fv_kernel_name(int kind);
