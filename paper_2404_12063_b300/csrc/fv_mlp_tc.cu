@@ -407,11 +407,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   // (one arrival per layer); the next tile's are requested as soon as their
   // buffers are dead in this tile
   uint64_t* ldbar = reinterpret_cast<uint64_t*>(sm + pl.o_bar + 24);
-#define FV_STASH (a.stash != nullptr && pl.n_stash > 0)
+  // (read from the kernel parameters at each use rather than held in registers)
+  auto stash_on = [&]() { return a.stash != nullptr && pl.n_stash > 0; };
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
     mbar_init(bar, 1);
-    if (FV_STASH) mbar_init(ldbar, pl.n_stash);
+    if (stash_on()) mbar_init(ldbar, pl.n_stash);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_load_weights<OP>(pl, a.params, sm);
@@ -526,9 +527,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   bool h0_ready = false;           // H_0 of this tile already in buf[0] (computed under the previous tile's MMAs)
   // with the stash, buf[0] takes a stashed layer (4 hidden layers) or H_0 (3)
-#define FV_STASH_BUF0 (FV_STASH && pl.n_stash == 2)
+  auto stash_buf0 = [&]() { return stash_on() && pl.n_stash == 2; };
   uint32_t ldstate = 0;            // bit 0: ldbar phase to wait for; bit 1: copies requested, not waited for
-  if (FV_STASH && blockIdx.x < n_tiles) {
+  if (stash_on() && blockIdx.x < n_tiles) {
     if (tid == 0) stash_request(blockIdx.x, 3);
     ldstate |= 2u;
   }
@@ -546,9 +547,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     // ---- forward recompute; the last hidden map's epilogue applies the output
     //      layer and the seeds and writes Zbar_{L-2} (its H is never stored)
     const int last = L - 2;
-    if (FV_STASH) {
+    if (stash_on()) {
       // stored layers from the forward kernel; maps 1 .. last-1 are not recomputed
-      if (!FV_STASH_BUF0 && !h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+      if (!stash_buf0() && !h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
       const bool ok = mbar_wait(ldbar, ldstate & 1u);
       ldstate = (ldstate & 1u) ^ 1u;
       if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); failed = true; break; }
@@ -649,12 +650,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         mma_commit(bar);
         // the next tile's stashed layers into buffers this tile no longer reads:
         // buf[1] from step 1 on (only H_0 in buf[0] is left), buf[0] at step 0
-        if (FV_STASH && has_next && i <= 1) {
+        if (stash_on() && has_next && i <= 1) {
           fence_proxy_async();
           stash_request(tile + gridDim.x, i == 1 ? 2 : 1);
         }
       }
-      if (FV_STASH && has_next && i <= 1) ldstate |= 2u;
+      if (stash_on() && has_next && i <= 1) ldstate |= 2u;
       // CUDA-core work on dead tiles while the tensor core runs: H_0 for map 1's
       // reverse step into buf[0] (H_2 there is dead once map 3's step is done),
       // and under map 0's step the next tile's H_0 (buf[0] held this tile's H_0,
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         bufH[0] = 0;
       }
       if (i == 0) {
-        h0_ready = last >= 1 && has_next && !FV_STASH_BUF0;
+        h0_ready = last >= 1 && has_next && !stash_buf0();
         if (h0_ready) layer0_store<OP>(pl, s_small, (float)nxt.x, (float)nxt.y, p, c0, sm + pl.o_buf[0]);
       }
       if (!sync_mma()) { failed = true; break; }
@@ -712,8 +713,6 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     }
   }
   if (ldstate & 2u) mbar_wait(ldbar, ldstate & 1u);   // after a failure: let requested copies land
-#undef FV_STASH_BUF0
-#undef FV_STASH
   // ---- write this CTA's gradient partials
   uint32_t* s_flags = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 12);
   if (tid == 0) *s_flags = wfirst;          // accumulators never written by this CTA
