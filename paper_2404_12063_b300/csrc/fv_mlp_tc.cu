@@ -1,5 +1,6 @@
 // tanh-MLP forward with tangents and its reverse sweep on the 5th-generation
-// tensor cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+// tensor cores (tcgen05, BF16 or FP16 operands, FP32 accumulation in tensor
+// memory).
 // Same mathematics as the CUDA-core kernels (Sec. 2.2 Eq. NN; forward-mode
 // tangents d/dx, d/dy; reverse sweep through the tanh rule):
 //
@@ -19,6 +20,10 @@
 // CUDA cores.  The bias of each hidden map rides in an extra weight column
 // that multiplies a constant-1 activation column, so the tensor core adds it
 // and the weight-gradient GEMM returns the bias gradient in that column.
+// When the reverse sweep follows (3 or 4 hidden layers), the forward kernel
+// also stores the hidden layers below the last hidden map per tile (the
+// activation stash) and the reverse kernel reads them back instead of
+// recomputing those maps.
 #include <algorithm>
 
 #include "fv_internal.cuh"
