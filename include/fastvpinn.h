@@ -113,7 +113,7 @@ int fv_ctx_enable_timing(fv_ctx ctx, int on);
 /* Activation stash of the tensor-core reverse sweep (FV_BF16 / FV_FP16
  * gradients of networks with 3 or 4 hidden layers), on by default: the
  * forward kernel also writes, per 128-point tile, the hidden activations of
- * the layers below the last hidden map (value and both tangents, 16-bit, 768
+ * the layers below the last hidden map (value and both tangents, 16-bit, 384
  * bytes per point and layer at width 50) to the context's workspace, and the
  * reverse kernel reads them by bulk copies instead of recomputing those maps
  * (Sec. 4.4's tensor form of the loss; the reverse sweep of the network in

@@ -599,7 +599,8 @@ def test_tensor_core_intermediates_elementwise(api, ctx, precision):
     assert rel(R, ref["R"]) < 2e-2
 
 
-@pytest.mark.parametrize("widths", [[2, 20, 1], [2, 24, 16, 1], [2, 30, 30, 30, 1], [2, 40, 40, 40, 40, 40, 1]])
+@pytest.mark.parametrize("widths", [[2, 20, 1], [2, 24, 16, 1], [2, 30, 30, 30, 1], [2, 40, 40, 40, 40, 40, 1],
+                                    [2, 24, 24, 24, 24, 24, 24, 1]])
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_network_depths(api, ctx, widths, precision):
     prob = _with(cfg("disc"), widths=widths, params=fi.random_bias_params(widths, 5, 1))
