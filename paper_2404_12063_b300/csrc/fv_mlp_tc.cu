@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   float accL[16];                  // output-layer weight gradient: this thread's columns, its points
 #pragma unroll
   for (int k = 0; k < 16; ++k) accL[k] = 0.f;
-  int bufH[2] = {-1, -1};
+  int bufH0 = -1, bufH1 = -1;      // layer held by activation tile 0 / 1
   const float sc = seed_scale(a.seed_absmax);   // adjoint scale (1 for BF16)
   const double inv_sc = 1.0 / (double)sc;
 
@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       fwd_epilogue_store(j, sm + pl.o_buf[j & 1]);
       publish();
     }
-    bufH[0] = upto >= 1 ? ((upto & 1) == 0 ? upto : upto - 1) : 0;
-    bufH[1] = upto >= 1 ? ((upto & 1) == 1 ? upto : upto - 1) : -1;
+    bufH0 = upto >= 1 ? ((upto & 1) == 0 ? upto : upto - 1) : 0;
+    bufH1 = upto >= 1 ? ((upto & 1) == 1 ? upto : upto - 1) : -1;
     return true;
   };
 
@@ -627,15 +627,15 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     }
     publish();
     // tiles holding H after the forward: H_j in buf[j & 1] for the two highest stored j
-    bufH[0] = -1; bufH[1] = -1;
-    if (last - 1 >= 0) bufH[(last - 1) & 1] = last - 1;
-    if (last - 2 >= 0) bufH[(last - 2) & 1] = last - 2;
+    bufH0 = -1; bufH1 = -1;
+    if (last - 1 >= 0) { if ((last - 1) & 1) bufH1 = last - 1; else bufH0 = last - 1; }
+    if (last - 2 >= 0) { if ((last - 2) & 1) bufH1 = last - 2; else bufH0 = last - 2; }
     // ---- reverse, map by map from the top
     for (int i = last; i >= 0 && !failed; --i) {
       uint32_t bsrc;
       int Kb;
       if (i >= 1) {
-        if (bufH[(i - 1) & 1] != i - 1) {
+        if ((((i - 1) & 1) ? bufH1 : bufH0) != i - 1) {
           if (!recompute(i - 1, x, y)) { failed = true; break; }
         }
         bsrc = su32(sm + pl.o_buf[(i - 1) & 1]);
@@ -665,9 +665,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       // reverse step into buf[0] (H_2 there is dead once map 3's step is done),
       // and under map 0's step the next tile's H_0 (buf[0] held this tile's H_0,
       // read by map 1's step only)
-      if (i == 2 && bufH[0] != 0) {
+      if (i == 2 && bufH0 != 0) {
         layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
-        bufH[0] = 0;
+        bufH0 = 0;
       }
       if (i == 0) {
         h0_ready = last >= 1 && has_next && !stash_buf0();
