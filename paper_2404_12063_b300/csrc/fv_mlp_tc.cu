@@ -265,6 +265,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   // loads are in flight during a tile; a ring of two shared slots.
   int* s_tl = reinterpret_cast<int*>(sm + pl.o_bar + 16);
   if (tid == 0) s_tl[0] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);
+  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
+  PointIn nxt;                                  // next tile's coordinates, loads in flight under the prologue
+  if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   tc_load_weights<OP>(pl, a.params, sm);
   fence_proxy_async();
   tc_fence_before();
@@ -275,9 +278,6 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   uint32_t phase = 0;
   bool failed = false;
   const int L = pl.L;
-  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
-  PointIn nxt;                                  // next tile's coordinates, loads in flight
-  if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   int64_t tile = blockIdx.x, next = s_tl[0];
   for (int it = 0; tile < n_tiles && !failed; ++it) {
     const int64_t gp = tile * kTile + p;
@@ -419,7 +419,22 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     mbar_init(bar, 1);
     if (stash_on()) mbar_init(ldbar, pl.n_stash);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the first tile's stashed layers, in flight under the weight prologue
+    if (stash_on() && blockIdx.x < (a.P_tot + kTile - 1) / kTile)
+      for (int j = pl.stash_lo; j < pl.stash_lo + pl.n_stash; ++j) {
+        const uint32_t bytes = 3u * 256u * (uint32_t)pl.WP[j];
+        mbar_expect_tx(ldbar, bytes);
+        bulk_load(sm + pl.o_buf[j & 1],
+                  a.stash + ((int64_t)blockIdx.x * pl.n_stash + (j - pl.stash_lo)) * (int64_t)pl.slot_bytes, bytes,
+                  ldbar, l2_evict_first());
+      }
   }
+  // this thread's point inputs for a tile (coordinates and seeds), kept as
+  // loaded so that the loads of the next tile stay in flight until first use
+  // (the first tile's under the weight prologue)
+  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
+  PointIn nxt;
+  if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   tc_load_weights<OP>(pl, a.params, sm);
   if (grp == 0) {  // layer-0 input tile: streams d/dx and d/dy are the constant unit vectors
     uint32_t ex[4] = {OP::pack(1.f, 0.f), 0, 0, 0};
@@ -525,19 +540,11 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     return true;
   };
 
-  // this thread's point inputs for a tile (coordinates and seeds), kept as
-  // loaded so that the loads of the next tile stay in flight until first use
-  const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
-  PointIn nxt;
-  if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
   bool h0_ready = false;           // H_0 of this tile already in buf[0] (computed under the previous tile's MMAs)
   // with the stash, buf[0] takes a stashed layer (4 hidden layers) or H_0 (3)
   auto stash_buf0 = [&]() { return stash_on() && pl.n_stash == 2; };
   uint32_t ldstate = 0;            // bit 0: ldbar phase to wait for; bit 1: copies requested, not waited for
-  if (stash_on() && blockIdx.x < n_tiles) {
-    if (tid == 0) stash_request(blockIdx.x, 3);
-    ldstate |= 2u;
-  }
+  if (stash_on() && blockIdx.x < n_tiles) ldstate |= 2u;   // the first tile's copies (requested above)
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     const float x = (float)nxt.x, y = (float)nxt.y;
     const float su = sc * nxt.s[0], sx = sc * nxt.s[1], sy = sc * nxt.s[2];
