@@ -56,7 +56,7 @@ struct TcPlan {
   int o_x;                  // layer-0 input tile (reverse kernel): 3 streams x 128 x 16
   int o_red;                // FP32 scratch [128][4] (output-layer partial sums)
   int o_bar;                // MMA mbarrier (8 B) + TMEM base (4 B) + flags (4 B) + two upcoming tile indices
-                            // (8 B, forward) or the activation-load mbarrier (8 B, reverse)
+                            // (8 B, forward) or the activation-load mbarrier (8 B, reverse) + a failure word
   int smem;
   int tmem_cols;
   int c_wbar[kMaxLayers];   // TMEM column of the weight-gradient accumulator of map i (reverse)
@@ -264,7 +264,10 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   // requested two ahead so that the atomic and the next tile's coordinate
   // loads are in flight during a tile; a ring of two shared slots.
   int* s_tl = reinterpret_cast<int*>(sm + pl.o_bar + 16);
-  if (tid == 0) s_tl[0] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);
+  // a wait that timed out marks this word; every thread reads it after the
+  // epilogue's barrier, so all leave the tile loop together
+  volatile uint32_t* s_fail = reinterpret_cast<volatile uint32_t*>(sm + pl.o_bar + 32);
+  if (tid == 0) { s_tl[0] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1); *s_fail = 0u; }
   const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
   PointIn nxt;                                  // next tile's coordinates, loads in flight under the prologue
   if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
@@ -304,9 +307,11 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
           issue_fwd(OP::fmt, tD, su32(buf), su32(sm + pl.o_w[i]), Kin, Nout, HP);
           mma_commit(bar);
         }
-        const bool ok = mbar_wait(bar, phase);
+        if (!mbar_wait(bar, phase)) {
+          *s_fail = 1u;
+          if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT);
+        }
         phase ^= 1;
-        if (__syncthreads_or(!ok)) { failed = true; if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); break; }
         tc_fence_after();
         const bool last = i == L - 2;
         const int wo = pl.w[i + 1];
@@ -363,6 +368,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
         if (!last) fence_proxy_async();
         tc_fence_before();
         __syncthreads();
+        if (*s_fail) { failed = true; break; }
       }
       if (failed) break;
     }
@@ -412,10 +418,14 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   // (one arrival per layer); the next tile's are requested as soon as their
   // buffers are dead in this tile
   uint64_t* ldbar = reinterpret_cast<uint64_t*>(sm + pl.o_bar + 24);
+  // an MMA wait that timed out marks this word; every thread reads it after the
+  // barrier that ends the step, so all leave the tile loop together
+  volatile uint32_t* s_fail = reinterpret_cast<volatile uint32_t*>(sm + pl.o_bar + 32);
   // (read from the kernel parameters at each use rather than held in registers)
   auto stash_on = [&]() { return a.stash != nullptr && pl.n_stash > 0; };
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
+    *s_fail = 0u;
     mbar_init(bar, 1);
     if (stash_on()) mbar_init(ldbar, pl.n_stash);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -462,12 +472,15 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   const float sc = seed_scale(a.seed_absmax);   // adjoint scale (1 for BF16)
   const double inv_sc = 1.0 / (double)sc;
 
-  auto sync_mma = [&]() -> bool {   // wait for the committed MMAs (all threads)
-    const bool ok = mbar_wait(bar, phase);
+  // wait for the committed MMAs (every thread for itself: the wait orders its
+  // own tensor-memory reads; a time-out is agreed on at the step's barrier)
+  auto wait_mma = [&]() {
+    if (!mbar_wait(bar, phase)) {
+      *s_fail = 1u;
+      if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT);
+    }
     phase ^= 1;
-    if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); return false; }
     tc_fence_after();
-    return true;
   };
   // tid 0: request stash layers j of tile t whose buffer (j & 1) is in `bufs`
   auto stash_request = [&](int64_t t, int bufs) {
@@ -531,9 +544,10 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     publish();
     for (int j = 1; j <= upto; ++j) {
       issue_fwd_map(j);
-      if (!sync_mma()) return false;
+      wait_mma();
       fwd_epilogue_store(j, sm + pl.o_buf[j & 1]);
       publish();
+      if (*s_fail) return false;
     }
     bufH0 = upto >= 1 ? ((upto & 1) == 0 ? upto : upto - 1) : 0;
     bufH1 = upto >= 1 ? ((upto & 1) == 1 ? upto : upto - 1) : -1;
@@ -567,19 +581,20 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); failed = true; break; }
       publish();
       issue_fwd_map(last);
-      if (!sync_mma()) { failed = true; break; }
+      wait_mma();
     } else if (last >= 1) {
       if (!h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
       publish();
       for (int i = 1; i < last; ++i) {
         issue_fwd_map(i);
-        if (!sync_mma()) { failed = true; break; }
+        wait_mma();
         fwd_epilogue_store(i, sm + pl.o_buf[i & 1]);
         publish();
+        if (*s_fail) { failed = true; break; }
       }
       if (failed) break;
       issue_fwd_map(last);
-      if (!sync_mma()) { failed = true; break; }
+      wait_mma();
     }
     {
       const int Nout = pl.WP[last], wo = pl.w[last + 1];
@@ -633,6 +648,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       }
     }
     publish();
+    if (*s_fail) { failed = true; break; }
     // tiles holding H after the forward: H_j in buf[j & 1] for the two highest stored j
     bufH0 = -1; bufH1 = -1;
     if (last - 1 >= 0) { if ((last - 1) & 1) bufH1 = last - 1; else bufH0 = last - 1; }
@@ -680,7 +696,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         h0_ready = last >= 1 && has_next && !stash_buf0();
         if (h0_ready) layer0_store<OP>(pl, s_small, (float)nxt.x, (float)nxt.y, p, c0, sm + pl.o_buf[0]);
       }
-      if (!sync_mma()) { failed = true; break; }
+      wait_mma();
       if (i >= 1) {
         // Zbar_{i-1} from Tbar_{i-1} (tensor memory) and H_{i-1} (shared tile), tanh rule
         const int K = pl.WP[i - 1];
@@ -722,6 +738,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         tc_fence_before();
         __syncthreads();
       }
+      if (*s_fail) { failed = true; break; }
     }
   }
   if (ldstate & 2u) mbar_wait(ldbar, ldstate & 1u);   // after a failure: let requested copies land
@@ -817,7 +834,7 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
     p->o_z = p->o_x = 0;
   }
   p->o_red = o; o += kTile * (HP / 16) * 3 * 4;
-  p->o_bar = o; o += 32;
+  p->o_bar = o; o += 48;
   p->smem = (o + 127) & ~127;
   int cols = 3 * HP;
   if (reverse) {
