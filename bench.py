@@ -606,7 +606,7 @@ def main():
     # the headline keeps the stored-G contraction (the G stream is the graded path)
     ok = [v for v in results if not v.endswith("_mf") and results[v]["within_tol"]]
     # FP16 is the 16-bit form that reaches the FP32 run's solution error in training (the metric's
-    # "at stated error"); BF16 is as fast but does not (profiles/precision_claim.md)
+    # "at stated error"); BF16 is as fast but does not
     head = "fp16" if "fp16" in ok else min(ok or [v for v in results if not v.endswith("_mf")],
                                               key=lambda v: results[v]["ms"])
     r = results[head]

@@ -229,19 +229,27 @@ int fv_loss_grad(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const f
 
 /* fv_loss_grad for callers that must not allocate device memory.  (This is a
  * service of the library; the paper has no counterpart.)  Some callers cannot
- * call cudaMalloc: code running in a host callback enqueued on a stream, which
- * may not make CUDA API calls; programs whose device memory is owned by a
- * framework pool that forbids raw allocations; and latency-critical loops that
+ * call cudaMalloc: programs whose device memory is owned by a framework pool
+ * that forbids raw allocations, and latency-critical training loops that
  * cannot afford cudaMalloc's implicit device-wide synchronisation.  This entry
  * point computes exactly what fv_loss_grad computes, with the same arguments,
  * but keeps every temporary in one fixed area of FV_NOALLOC_SCRATCH_BYTES that
  * is compiled into the library: each device that loads the library holds that
  * area until the process exits.  Nothing is allocated per call.
+ *   - Caller: ordinary host code.  The call itself makes CUDA runtime calls
+ *     (cudaSetDevice, the area's address lookup, cudaMemsetAsync, kernel
+ *     launches, event records), so it cannot be made where the CUDA API is
+ *     not allowed, such as inside a host function enqueued on a stream.
  *   - Size limit: problems whose temporaries exceed the area (roughly a million
  *     quadrature points in FP32, fewer in FP64 or with large networks) are
- *     rejected with FV_ERR_UNSUPPORTED and a message giving both sizes.
+ *     rejected with FV_ERR_UNSUPPORTED and a message giving both sizes.  For the
+ *     16-bit tensor-core forms the activation stash is left out when it does not
+ *     fit (the reverse sweep then recomputes the hidden layers; same results).
  *   - Set-up: the first call on a device looks up the area's device address
- *     (once per device); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress, once per device, cached); make that first call
+ *     before any stream capture.  A device reset (cudaDeviceReset) unloads the
+ *     library's module and leaves the cached address stale: do not call this
+ *     entry point on a device after resetting it.
  *   - Sharing: every call on a device uses the same area, and the area keeps
  *     the last call's contents.  Calls whose kernels overlap on the GPU (for
  *     example on two streams, or from two contexts) race on it; issue them one

@@ -226,8 +226,23 @@ class Problem:
             raise ValueError("params must be a contiguous CUDA %s tensor of %d values"
                              % (self.dtype, self.net.n_params))
 
+    def _check_outputs(self, params: torch.Tensor, grad: Optional[torch.Tensor], out: Optional[torch.Tensor],
+                       n_out: int):
+        """The library writes n_params values to grad and n_out doubles to out
+        without bounds: a short, strided, wrongly typed or host tensor would be
+        an out-of-bounds device write, so it is refused here."""
+        if grad is not None and (not grad.is_cuda or grad.device != params.device or grad.dtype != self.dtype
+                                 or not grad.is_contiguous() or grad.numel() != self.net.n_params):
+            raise ValueError("grad must be a contiguous %s tensor of %d values on %s"
+                             % (self.dtype, self.net.n_params, params.device))
+        if out is not None and (not out.is_cuda or out.device != params.device or out.dtype != torch.float64
+                                or not out.is_contiguous() or out.numel() < n_out):
+            raise ValueError("out must be a contiguous float64 tensor of at least %d values on %s"
+                             % (n_out, params.device))
+
     def loss(self, params: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         self._check_params(params)
+        self._check_outputs(params, None, out, 4)
         out = self.out if out is None else out
         o = self.opts()
         N.call("fv_loss", self.ctx.h, self.mesh.h, self.forcing.h, self.bc.h if self.bc else None,
@@ -238,6 +253,7 @@ class Problem:
                   out: Optional[torch.Tensor] = None):
         """Returns (out, grad): out = (L, Lv, Lb, Ls, dL/deps) on the device."""
         self._check_params(params)
+        self._check_outputs(params, grad, out, 5)
         grad = torch.empty_like(params) if grad is None else grad
         out = self.out if out is None else out
         o = self.opts()
@@ -250,6 +266,9 @@ class Problem:
         library's fixed scratch area (for callers that cannot allocate device
         memory); grad and out must be supplied."""
         self._check_params(params)
+        if grad is None or out is None:
+            raise ValueError("loss_grad_noalloc needs caller-supplied grad and out tensors")
+        self._check_outputs(params, grad, out, 5)
         o = self.opts()
         N.call("fv_loss_grad_noalloc", self.ctx.h, self.mesh.h, self.forcing.h, self.bc.h if self.bc else None,
                C.byref(self.net.desc), _ptr(params), C.byref(o), _ptr(grad), _ptr(out))
@@ -272,6 +291,7 @@ class Problem:
     def inverse_step(self, params: torch.Tensor, eps_dev: torch.Tensor, adam: Optional["Adam"], lr: float,
                      grad: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None):
         self._check_params(params)
+        self._check_outputs(params, grad, out, 5)
         grad = torch.empty_like(params) if grad is None else grad
         out = self.out if out is None else out
         o = self.opts(eps_dev)

@@ -620,7 +620,8 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on `device` (which must be current).
 // In host code the array's name only stands in for the symbol, so the
-// address is looked up once per device and cached.
+// address is looked up once per device and cached; a device reset
+// (cudaDeviceReset) unloads the module and leaves the cached address stale.
 int noalloc_scratch(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) {
     set_error("fv_loss_grad_noalloc: device %d out of range", device);

@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kCThreads) contract_staged(ContractArgs a) {
 // element, G read straight from global memory in both passes.
 template <class R, class Gt>
 __global__ void __launch_bounds__(kThreads) contract_direct(ContractArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   double* s_R = reinterpret_cast<double*>(smem);     // [Nt]
   double* s_red = s_R + a.Nt;                         // [kWarps][4]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

@@ -264,10 +264,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   // requested two ahead so that the atomic and the next tile's coordinate
   // loads are in flight during a tile; a ring of two shared slots.
   int* s_tl = reinterpret_cast<int*>(sm + pl.o_bar + 16);
-  // a wait that timed out marks this word; every thread reads it after the
-  // epilogue's barrier, so all leave the tile loop together
-  volatile uint32_t* s_fail = reinterpret_cast<volatile uint32_t*>(sm + pl.o_bar + 32);
-  if (tid == 0) { s_tl[0] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1); *s_fail = 0u; }
+  if (tid == 0) s_tl[0] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);
   const int64_t n_tiles = (a.P_tot + kTile - 1) / kTile;
   PointIn nxt;                                  // next tile's coordinates, loads in flight under the prologue
   if (blockIdx.x < n_tiles) point_fetch(a, blockIdx.x * kTile + p, nxt);
@@ -280,6 +277,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   const uint32_t tRow = tD + ((uint32_t)(q4 * 32) << 16);
   uint32_t phase = 0;
   bool failed = false;
+  // this thread's MMA wait timed out; the threads agree on it at the barrier
+  // that ends each map (a reduction barrier), so all leave the tile loop together
+  bool tfail = false;
   const int L = pl.L;
   int64_t tile = blockIdx.x, next = s_tl[0];
   for (int it = 0; tile < n_tiles && !failed; ++it) {
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
           mma_commit(bar);
         }
         if (!mbar_wait(bar, phase)) {
-          *s_fail = 1u;
+          tfail = true;
           if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT);
         }
         phase ^= 1;
@@ -367,8 +367,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
         }
         if (!last) fence_proxy_async();
         tc_fence_before();
-        __syncthreads();
-        if (*s_fail) { failed = true; break; }
+        if (__syncthreads_or(tfail)) { failed = true; break; }
       }
       if (failed) break;
     }
@@ -418,14 +417,10 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   // (one arrival per layer); the next tile's are requested as soon as their
   // buffers are dead in this tile
   uint64_t* ldbar = reinterpret_cast<uint64_t*>(sm + pl.o_bar + 24);
-  // an MMA wait that timed out marks this word; every thread reads it after the
-  // barrier that ends the step, so all leave the tile loop together
-  volatile uint32_t* s_fail = reinterpret_cast<volatile uint32_t*>(sm + pl.o_bar + 32);
   // (read from the kernel parameters at each use rather than held in registers)
   auto stash_on = [&]() { return a.stash != nullptr && pl.n_stash > 0; };
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
-    *s_fail = 0u;
     mbar_init(bar, 1);
     if (stash_on()) mbar_init(ldbar, pl.n_stash);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -473,10 +468,13 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   const double inv_sc = 1.0 / (double)sc;
 
   // wait for the committed MMAs (every thread for itself: the wait orders its
-  // own tensor-memory reads; a time-out is agreed on at the step's barrier)
+  // own tensor-memory reads); a time-out sets this thread's flag, which the
+  // threads agree on at the reduction barrier that ends the step (the flag
+  // stays set, so every later barrier agrees too)
+  bool tfail = false;
   auto wait_mma = [&]() {
     if (!mbar_wait(bar, phase)) {
-      *s_fail = 1u;
+      tfail = true;
       if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT);
     }
     phase ^= 1;
@@ -492,10 +490,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
                 ldbar, l2_evict_first());
     }
   };
-  auto publish = [&]() {            // make this thread's shared stores visible to the tensor core
+  // make this thread's shared stores visible to the tensor core; true when
+  // some thread's MMA wait has timed out
+  auto publish = [&]() -> bool {
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();
+    return __syncthreads_or(tfail) != 0;
   };
   auto issue_fwd_map = [&](int i) {
     if (tid == 0) {
@@ -541,13 +541,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   // recompute H_0 .. H_upto into the two activation tiles (H_j -> buf[j & 1])
   auto recompute = [&](int upto, float x, float y) -> bool {
     layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
-    publish();
+    if (publish()) return false;
     for (int j = 1; j <= upto; ++j) {
       issue_fwd_map(j);
       wait_mma();
       fwd_epilogue_store(j, sm + pl.o_buf[j & 1]);
-      publish();
-      if (*s_fail) return false;
+      if (publish()) return false;
     }
     bufH0 = upto >= 1 ? ((upto & 1) == 0 ? upto : upto - 1) : 0;
     bufH1 = upto >= 1 ? ((upto & 1) == 1 ? upto : upto - 1) : -1;
@@ -579,18 +578,17 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       const bool ok = mbar_wait(ldbar, ldstate & 1u);
       ldstate = (ldstate & 1u) ^ 1u;
       if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); failed = true; break; }
-      publish();
+      if (publish()) { failed = true; break; }
       issue_fwd_map(last);
       wait_mma();
     } else if (last >= 1) {
       if (!h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
-      publish();
+      if (publish()) { failed = true; break; }
       for (int i = 1; i < last; ++i) {
         issue_fwd_map(i);
         wait_mma();
         fwd_epilogue_store(i, sm + pl.o_buf[i & 1]);
-        publish();
-        if (*s_fail) { failed = true; break; }
+        if (publish()) { failed = true; break; }
       }
       if (failed) break;
       issue_fwd_map(last);
@@ -647,8 +645,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         }
       }
     }
-    publish();
-    if (*s_fail) { failed = true; break; }
+    if (publish()) { failed = true; break; }
     // tiles holding H after the forward: H_j in buf[j & 1] for the two highest stored j
     bufH0 = -1; bufH1 = -1;
     if (last - 1 >= 0) { if ((last - 1) & 1) bufH1 = last - 1; else bufH0 = last - 1; }
@@ -733,12 +730,11 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
             st8(zb + 512 * K, K, p, cc, py);
           }
         }
-        publish();
+        if (publish()) { failed = true; break; }
       } else {
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(tfail)) { failed = true; break; }
       }
-      if (*s_fail) { failed = true; break; }
     }
   }
   if (ldstate & 2u) mbar_wait(ldbar, ldstate & 1u);   // after a failure: let requested copies land
