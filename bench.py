@@ -119,54 +119,101 @@ def contract_bytes(mesh, gsize, fsize=4):
 
 
 # ----------------------------------------------------------------------------- clocks
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
 class ClockSampler:
-    def __init__(self, index=0):
-        self.index = index
+    """SM clock, its maximum, board power and the throttle reasons, sampled
+    every 20 ms from a thread while the GPU is under load (NVML reads only;
+    nothing is set).  Falls back to a line-buffered nvidia-smi loop with the
+    query fields this driver accepts."""
+
+    def __init__(self, cuda_index=0):
+        self.cuda_index = cuda_index
+        self.samples = []            # (sm_mhz, max_mhz, power_w, reasons)
+        self.thread = None
         self.proc = None
-        self.path = None
+        self.stop_flag = False
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.cuda_index)
+            bus = "%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), pr.pci_bus_id, pr.pci_device_id)
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.cuda_index)
+
+    def _nvml_loop(self, nv, h):
+        bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
+                "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
+                "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
+                "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
+        mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+        while not self.stop_flag:
+            try:
+                sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
+                pw = nv.nvmlDeviceGetPowerUsage(h) / 1e3
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.samples.append((sm, mx, pw, [n for n, b in bits.items() if r & b]))
+            except Exception:
+                pass
+            time.sleep(0.02)
 
     def start(self):
+        import threading
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            nv, h = self._nvml_handle()
+            self.kind = "nvml"
+            self.thread = threading.Thread(target=self._nvml_loop, args=(nv, h), daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.thread = None
+        try:     # nvidia-smi: keep only the fields this driver accepts, line-buffered output
+            fields = ["clocks.sm", "clocks.max.sm", "power.draw"] + ["clocks_event_reasons." + n for n in CLOCK_REASONS]
+            ok = [f for f in fields if subprocess.run(["nvidia-smi", "-i", str(self.cuda_index), "--query-gpu=" + f,
+                                                       "--format=csv,noheader,nounits"],
+                                                      capture_output=True).returncode == 0]
+            self.fields = ok
+            self.proc = subprocess.Popen(["stdbuf", "-oL", "nvidia-smi", "-i", str(self.cuda_index),
+                                          "--query-gpu=" + ",".join(ok), "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.kind = "nvidia-smi"
         except Exception:
             self.proc = None
 
     def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        if not self.proc:
-            return out
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=2)
+        elif self.proc is not None:
+            self.proc.terminate()
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        os.unlink(self.path)
-        if sm:
-            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                   "samples": len(sm)}
+                txt, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                txt = ""
+            for line in (txt or "").splitlines():
+                d = dict(zip(self.fields, [x.strip() for x in line.split(",")]))
+                try:
+                    sm = float(d["clocks.sm"])
+                    mx = float(d.get("clocks.max.sm", "nan"))
+                    pw = float(d.get("power.draw", "nan"))
+                except (KeyError, ValueError):
+                    continue
+                rs = [n for n in CLOCK_REASONS if d.get("clocks_event_reasons." + n, "").lower().startswith("active")]
+                self.samples.append((sm, mx, pw, rs))
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.samples),
+               "source": getattr(self, "kind", None)}
+        if self.samples:
+            sm = [x[0] for x in self.samples]
+            out.update({"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm),
+                        "sm_max_mhz": max(x[1] for x in self.samples),
+                        "power_w_max": max(x[2] for x in self.samples),
+                        "reasons": sorted({r for x in self.samples for r in x[3]})})
         return out
 
 
@@ -218,14 +265,48 @@ def oracle_sample(prob, target_s=10.0, max_elems=None):
         n = min(prob.mesh.n_elements, int(n * max(2.0, (target_s / 3) / max(dt, 1e-3))))
 
 
+def workload_config(prob):
+    """The bench line's `config`: the workload alone, identical for both arms
+    (the GPU form and its precision are reported beside it, not in it)."""
+    nq, nt, ne = prob.quad_order ** 2, prob.test_order ** 2, prob.mesh.n_elements
+    w = prob.widths
+    hidden = w[1:-1]
+    mlp = "%d-%dx%d-%d" % (w[0], hidden[0], len(hidden), w[-1]) if len(set(hidden)) == 1 else "-".join(map(str, w))
+    g16, g32 = ne * 2 * nt * nq * 2, ne * 2 * nt * nq * 4
+    return {"workload": prob.name, "elements": ne, "Q": prob.quad_order, "T": prob.test_order,
+            "quad_points": prob.n_points, "boundary_points": len(prob.bd_xy), "mlp": mlp,
+            "l2": "inputs larger than L2 (126 MB): G is %.0f MB in BF16, %.0f MB in FP32" % (g16 / 1e6, g32 / 1e6),
+            "parallelism": "replicas"}
+
+
+REF_BUDGET_S = 150.0     # the reference arm's timed oracle work is kept within a few minutes
+
+
 def run_reference(args, prob):
-    """The oracle as it stands on the host cores: each step one loss+grad of a
-    bounded element sample of the workload, scaled to whole-workload evals/s."""
+    """The oracle as it stands on the host cores.  Each step is one loss+grad
+    of the whole workload when warm-up + steps fit in a few minutes (one
+    evaluation takes ~2 s on 16 cores); otherwise each step is the same
+    bounded element sample, and `value` scales its points/s to whole-workload
+    evaluations/s.  `ms_per_step` is the time actually measured per step."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
-    sub, b, _, nth = oracle_sample(prob, target_s=max(3.0, 60.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
+    import oracle
+    import fv_inputs as fi
+    nth = os.cpu_count() or 1
+    n_evals = args.steps + args.warmup
+    full = prob.n_points + len(prob.bd_xy)
+    b = oracle.Bound(prob)
+    t0 = time.perf_counter()
+    b.loss_grad(prob.params, n_threads=nth)        # the first warm-up step, also sizes the run
+    t_full = time.perf_counter() - t0
+    sub = prob
+    if t_full * n_evals > REF_BUDGET_S:
+        n = max(16, int(prob.mesh.n_elements * REF_BUDGET_S / (t_full * n_evals)))
+        sub = fi.Problem(**{**prob.__dict__, "mesh": prob.mesh.subset(0, n)})
+        b = oracle.Bound(sub)
+        b.loss_grad(prob.params, n_threads=nth)
+    for _ in range(args.warmup - 1):
         b.loss_grad(prob.params, n_threads=nth)
     ts = []
     for _ in range(args.steps):
@@ -234,17 +315,19 @@ def run_reference(args, prob):
         ts.append(time.perf_counter() - t0)
     t = statistics.median(ts)
     pts = sub.n_points + len(sub.bd_xy)
-    full = prob.n_points + len(prob.bd_xy)
     evals = (pts / t) / full
-    sample = "%d of %d elements (%d quad + %d boundary points), FP64 oracle, %d OpenMP threads" % (
-        sub.mesh.n_elements, prob.mesh.n_elements, sub.n_points, len(sub.bd_xy), nth)
+    if sub is prob:
+        sample = "the whole workload per step (%d elements, %d quad + %d boundary points), FP64 oracle, " \
+                 "%d OpenMP threads" % (prob.mesh.n_elements, prob.n_points, len(prob.bd_xy), nth)
+    else:
+        sample = "%d of %d elements per step (%d quad + %d boundary points), FP64 oracle, %d OpenMP threads; " \
+                 "value scaled to whole-workload evaluations" % (sub.mesh.n_elements, prob.mesh.n_elements,
+                                                                 sub.n_points, len(sub.bd_xy), nth)
     line = {"impl": "reference", "metric": METRIC, "value": evals, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full / (pts / t),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": prob.name, "quad_points": prob.n_points,
-                                            "elements": prob.mesh.n_elements, "Q": prob.quad_order,
-                                            "T": prob.test_order, "mlp": "2-50x4-1"},
-            "quad_pts_per_s": pts / t,
+            "data": "synthetic", "config": workload_config(prob),
+            "quad_pts_per_s": evals * prob.n_points,
             "cpu_baseline": {"value": evals, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample},
             "e2e": {"value": evals, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -557,7 +640,6 @@ def main():
         torch.cuda.synchronize()
         barrier(world)
         ms = time_steps(torch, stream, fn, args.steps)
-        cl = clocks.stop()
         ms = max_over_ranks(ms, world, torch.device("cuda", local))
         # per-kernel times over a second timed pass (CUDA events around each launch on this stream)
         ctx.reset_kernel_times()
@@ -581,6 +663,7 @@ def main():
         for _ in range(3):
             e2e_step()
         ms_e2e = time_steps(torch, stream, e2e_step, args.steps)
+        cl = clocks.stop()                # samples span the warm-up, timed, per-kernel and end-to-end passes
         ms_e2e = max_over_ranks(ms_e2e, world, torch.device("cuda", local))
         results[v] = dict(ms=ms, kt=kt, clocks=cl, ms_e2e=ms_e2e, loss=float(out[0]), pb=pb,
                           bytes_h2d=h_params.numel() * h_params.element_size(),
@@ -684,10 +767,8 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32/f32-accum", "bf16": "bf16/f32-accum",
                                        "fp16": "f16/f32-accum", "fp64": "f64"}[head],
         "data": "synthetic",
-        "config": {"workload": prob.name, "elements": prob.mesh.n_elements, "Q": prob.quad_order,
-                   "T": prob.test_order, "quad_points": prob.n_points, "boundary_points": len(prob.bd_xy),
-                   "mlp": "2-50x4-1", "variant": head, "g_storage": "bf16" if g16 else "fp32",
-                   "l2": "inputs larger than L2 (G = %.0f MB)" % (gbytes / 1e6), "parallelism": "replicas"},
+        "config": workload_config(prob),
+        "variant": {"name": head, "g_storage": "bf16" if g16 else "fp32"},
         "quad_pts_per_s": world * prob.n_points * 1e3 / r["ms"],
         "variants": variants_out,
         "g_build_ms": {"fp32": meshes["fp32_ms"], "bf16": meshes["bf16_ms"]},

@@ -57,9 +57,11 @@ struct TcPlan {
   int o_red;                // FP32 scratch [128][4] (output-layer partial sums)
   int o_bar;                // MMA mbarrier (8 B) + TMEM base (4 B) + flags (4 B) + two upcoming tile indices
                             // (8 B, forward) or the activation-load mbarrier (8 B, reverse) + a failure word
+  int o_tab;                // per-map constants copied to shared memory (TcTab)
   int smem;
   int tmem_cols;
   int c_wbar[kMaxLayers];   // TMEM column of the weight-gradient accumulator of map i (reverse)
+  int c_part;               // reverse: partial weight-gradient accumulator (HP columns), 0: none
   // Activation stash (networks of 3 or 4 hidden layers): H_j for j = stash_lo ..
   // L-3, the stored layers below the last hidden map, written per tile by the
   // forward kernel and read by the reverse kernel instead of recomputing maps
@@ -82,6 +84,29 @@ struct TcArgs {
   uint8_t* stash;           // [n_tiles][n_stash][slot_bytes] activation tiles, or null (recompute)
   int* err;
 };
+
+// The plan's per-map arrays in shared memory.  Kernel parameters indexed with a
+// run-time map index are loads from the constant bank at a computed address,
+// which cost hundreds of cycles each on the MMA-issue path when they miss the
+// constant cache; the copies in shared memory cost a shared-memory load.
+struct TcTab {
+  int w[kMaxLayers + 1], WP[kMaxLayers], o_w[kMaxLayers], c_wbar[kMaxLayers], off[kMaxLayers], o_buf[2];
+};
+__device__ __forceinline__ const TcTab* tc_tab_init(const TcPlan& pl, uint8_t* sm) {
+  TcTab* t = reinterpret_cast<TcTab*>(sm + pl.o_tab);
+  const int i = threadIdx.x;
+  if (i <= kMaxLayers) {
+    t->w[i] = pl.w[i];
+    if (i < kMaxLayers) {
+      t->WP[i] = pl.WP[i];
+      t->o_w[i] = pl.o_w[i];
+      t->c_wbar[i] = pl.c_wbar[i];
+      t->off[i] = pl.off[i];
+    }
+    if (i < 2) t->o_buf[i] = pl.o_buf[i];
+  }
+  return t;
+}
 
 // Power-of-two scale 2^-e with max|seed| <= 2^e, so scaled seeds lie in [-1, 1]
 // (exact to apply and to undo).
@@ -155,6 +180,8 @@ __device__ __forceinline__ void point_fetch(const TcArgs& a, int64_t gp, PointIn
 }
 
 // Layer 0 on CUDA cores: H_0 row p (3 streams), this thread's 16 columns.
+// Columns past the width have zero weights, so their tangents are 0; the bias
+// column (index w1) is then set to (1, 0, 0) by the warps that hold it.
 template <class OP>
 __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_small, float x, float y, int p,
                                              int c0, uint8_t* buf) {
@@ -162,79 +189,140 @@ __device__ __forceinline__ void layer0_store(const TcPlan& pl, const float* s_sm
   if (c0 >= K0) return;
 #pragma unroll
   for (int sc = 0; sc < 16; sc += 8) {
+    const int cc = c0 + sc;
+    float wx[8], wy[8], b0[8];
+#pragma unroll
+    for (int q = 0; q < 8; q += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(s_small + cc + q);
+      const float4 b = *reinterpret_cast<const float4*>(s_small + HP + cc + q);
+      const float4 c = *reinterpret_cast<const float4*>(s_small + 2 * HP + cc + q);
+      wx[q] = a.x; wx[q + 1] = a.y; wx[q + 2] = a.z; wx[q + 3] = a.w;
+      wy[q] = b.x; wy[q + 1] = b.y; wy[q + 2] = b.z; wy[q + 3] = b.w;
+      b0[q] = c.x; b0[q + 1] = c.y; b0[q + 2] = c.z; b0[q + 3] = c.w;
+    }
     uint32_t pv[4], px[4], py[4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
       float tv[2], tx[2], ty[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int o = c0 + sc + j + h;
-        const float wx = s_small[o], wy = s_small[HP + o];
-        const float t = tanh_fast(fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o])));
+        const float t = tanh_fast(fmaf(wx[j + h], x, fmaf(wy[j + h], y, b0[j + h])));
         const float sd = fmaf(-t, t, 1.f);
-        tv[h] = o == w1 ? 1.f : t;
-        tx[h] = o == w1 ? 0.f : sd * wx;
-        ty[h] = o == w1 ? 0.f : sd * wy;
+        tv[h] = t;
+        tx[h] = sd * wx[j + h];
+        ty[h] = sd * wy[j + h];
       }
       pv[j >> 1] = OP::pack(tv[0], tv[1]);
       px[j >> 1] = OP::pack(tx[0], tx[1]);
       py[j >> 1] = OP::pack(ty[0], ty[1]);
     }
-    st8(buf, K0, p, c0 + sc, pv);
-    st8(buf + 256 * K0, K0, p, c0 + sc, px);
-    st8(buf + 512 * K0, K0, p, c0 + sc, py);
+    if (w1 >= cc && w1 < cc + 8) set_bias_col<OP>(w1 - cc, pv, px, py);
+    st8(buf, K0, p, cc, pv);
+    st8(buf + 256 * K0, K0, p, cc, px);
+    st8(buf + 512 * K0, K0, p, cc, py);
   }
 }
 
-// The three streams' MMAs are issued round-robin (K step outer, stream inner).
+// MMA issue.  One thread issues a tcgen05.mma about every 60 cycles, while the
+// tensor core completes an M = 128, N = 64, K = 16 product in about 50 (M = 64:
+// about 33), so the MMAs of a step are spread over the lane 0 of warps 0..3 (one
+// per SM sub-partition), each writing its own accumulator; every step commits
+// from all four threads to one mbarrier (arrival count 4; a thread with nothing
+// to issue commits an empty set).  Descriptors are formed once per chain and
+// advanced by adding the byte offset / 16 to the start-address field (shared
+// memory below 256 KB keeps it inside its 14 bits).
+constexpr uint32_t kIssuers = 4;
 
-// Forward MMAs of map i: D_s (columns s*HP) = H_{i-1,s} W_i^T, K = Kin, N = Nout.
-__device__ __forceinline__ void issue_fwd(uint32_t fmt, uint32_t tD, uint32_t abuf, uint32_t wbuf, int Kin, int Nout,
-                                          int HP) {
+// A chain of n MMAs into D: operand descriptors advance by da / db per step.
+__device__ __forceinline__ void mma_chain(uint32_t tD, uint64_t a, uint32_t da, uint64_t b, uint32_t db, uint32_t id,
+                                          int n, bool first) {
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    mma_bf16(tD, a, b, id, (first && k == 0) ? 0u : 1u);
+    a += da;
+    b += db;
+  }
+}
+
+// Forward MMAs of map i for stream s: D_s (columns s*HP) = H_{i-1,s} W_i^T, K = Kin, N = Nout.
+__device__ __forceinline__ void issue_fwd_stream(uint32_t fmt, uint32_t tD, uint32_t abuf, uint32_t wbuf, int Kin,
+                                                 int Nout, int HP, int s) {
   const uint32_t id = idesc_f16(fmt, 128, Nout, 0, 0);
-  for (int kk = 0; kk < Kin / 16; ++kk)
-    for (int s = 0; s < 3; ++s) {
-      const uint64_t ad = sdesc(abuf + s * 256 * Kin + kk * 256, 128, Kin * 16);
-      const uint64_t bd = sdesc(wbuf + kk * 256, 128, Kin * 16);
-      mma_bf16(tD + s * HP, ad, bd, id, kk > 0);
-    }
+  mma_chain(tD + s * HP, sdesc(abuf + s * 256 * Kin, 128, Kin * 16), 256 >> 4, sdesc(wbuf, 128, Kin * 16), 256 >> 4, id,
+            Kin / 16, true);
 }
 
-// Reverse step of map i >= 1 (all weight-gradient MMAs, then all adjoint
-// products, one commit: issuing the adjoint products first with a commit of
-// their own, or mixing the two shapes in the issue order, slows the pipe):
-//   Wbar_i (M = 64 rows o, N = Kin) += sum over streams and points of Zbar^T B,
-//     both read MN-major; K runs over 3 streams x 128 points (one chain);
-//   Tbar_s (columns s*HP) = Zbar_s W_i: A = Zbar (K-major, K = Nout), B = W_i
-//     read MN-major (N = Kin), streams round-robin.
-__device__ __forceinline__ void issue_reverse(uint32_t fmt, uint32_t tD, uint32_t tW, uint32_t zbuf, uint32_t wbuf,
-                                              uint32_t bbuf, int Kin, int Nout, int HP, bool first) {
-  const uint32_t idw = idesc_f16(fmt, 64, Kin, 1, 1);
-  for (int w = 0; w < 3 * (kTile / 16); ++w) {
-    const int s = w / (kTile / 16), ps = w % (kTile / 16);
-    const uint64_t ad = sdesc(zbuf + s * 256 * Nout + ps * 2 * Nout * 16, Nout * 16, 128);
-    const uint64_t bd = sdesc(bbuf + s * 256 * Kin + ps * 2 * Kin * 16, Kin * 16, 128);
-    mma_bf16(tW, ad, bd, idw, (first && w == 0) ? 0u : 1u);
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float v[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Steps [k0, k1) of a weight-gradient chain (step k: stream k / 8, point block k % 8;
+// 24 steps = K of 3 streams x 128 points) into accumulator tAcc.  Wbar_i reads
+// H_{i-1} (Kin columns); Wbar_0 (w0) reads the layer-0 input: the value stream
+// (x, y, 1) per point block and the constant tangent blocks.
+__device__ __forceinline__ void wbar_chain_part(uint32_t fmt, uint32_t tAcc, uint32_t zbuf, int Nout, uint32_t bbuf,
+                                                int Kin, bool w0, int k0, int k1, bool zero_first) {
+  const uint32_t id = w0 ? idesc_f16(fmt, 64, 16, 1, 1) : idesc_f16(fmt, 64, Kin, 1, 1);
+  for (int s = k0 >> 3; s <= (k1 - 1) >> 3; ++s) {
+    const int p0 = s == (k0 >> 3) ? (k0 & 7) : 0;
+    const int p1 = s == ((k1 - 1) >> 3) ? ((k1 - 1) & 7) + 1 : 8;
+    const uint64_t a = sdesc(zbuf + s * 256 * Nout + p0 * 2 * Nout * 16, Nout * 16, 128);
+    uint64_t b;
+    uint32_t db;
+    if (w0) {
+      b = s ? sdesc(bbuf + 256 * 16 + (s - 1) * 512, 256, 128) : sdesc(bbuf + p0 * 2 * 16 * 16, 256, 128);
+      db = s ? 0u : ((2 * 16 * 16) >> 4);
+    } else {
+      b = sdesc(bbuf + s * 256 * Kin + p0 * 2 * Kin * 16, Kin * 16, 128);
+      db = (2 * Kin * 16) >> 4;
+    }
+    mma_chain(tAcc, a, (2 * Nout * 16) >> 4, b, db, id, p1 - p0, zero_first && s == (k0 >> 3));
   }
-  const uint32_t idt = idesc_f16(fmt, 128, Kin, 0, 1);
-  for (int kk = 0; kk < Nout / 16; ++kk)
-    for (int s = 0; s < 3; ++s) {
-      const uint64_t at = sdesc(zbuf + s * 256 * Nout + kk * 256, 128, Nout * 16);
-      const uint64_t bt = sdesc(wbuf + kk * 2 * Kin * 16, Kin * 16, 128);
-      mma_bf16(tD + s * HP, at, bt, idt, kk > 0);
-    }
 }
 
-// Reverse step of map 0 (inputs x, y, 1 in a 16-column tile): Wbar_0, one chain.
-__device__ __forceinline__ void issue_wbar0(uint32_t fmt, uint32_t tW, uint32_t zbuf, int Kz, uint32_t xbuf,
-                                            bool first) {
+// Reverse step of map i >= 1:
+//   Tbar_s (columns s*HP) = Zbar_s W_i: A = Zbar (K-major, K = Nout), B = W_i read
+//     MN-major (N = Kin); stream s on issuer s (s = 0, 1, 2);
+//   Wbar_i (M = 64 rows o, N = Kin) += sum over streams and points of Zbar^T B,
+//     both read MN-major; K runs over 3 streams x 128 points.  With a partial
+//     accumulator (tP) the chain is split: steps 0..11 into Wbar_i on issuer 3,
+//     steps 12..23 into the partial on issuer 2, and the epilogue threads add
+//     the partial into Wbar_i once both have completed; otherwise one chain on
+//     issuer 3.
+__device__ __forceinline__ void issue_reverse(uint32_t fmt, uint32_t tD, uint32_t tW, uint32_t tP, bool split,
+                                              uint32_t zbuf, uint32_t wbuf, uint32_t bbuf, int Kin, int Nout, int HP,
+                                              bool first, int issuer) {
+  if (issuer < 3) {
+    const int s = issuer;
+    const uint32_t idt = idesc_f16(fmt, 128, Kin, 0, 1);
+    mma_chain(tD + s * HP, sdesc(zbuf + s * 256 * Nout, 128, Nout * 16), 256 >> 4, sdesc(wbuf, Kin * 16, 128),
+              (2 * Kin * 16) >> 4, idt, Nout / 16, true);
+  }
+  if (issuer == 3) wbar_chain_part(fmt, tW, zbuf, Nout, bbuf, Kin, false, 0, split ? 12 : 24, first);
+  if (issuer == 2 && split) wbar_chain_part(fmt, tP, zbuf, Nout, bbuf, Kin, false, 12, 24, true);
+}
+
+// Reverse step of map 0 (inputs x, y, 1 in a 16-column tile): Wbar_0, split as above.
+__device__ __forceinline__ void issue_wbar0(uint32_t fmt, uint32_t tW, uint32_t tP, bool split, uint32_t zbuf, int Kz,
+                                            uint32_t xbuf, bool first, int issuer) {
+  // the tangent streams of the layer-0 input tile are the full 128-point tiles of this kernel
   const uint32_t id = idesc_f16(fmt, 64, 16, 1, 1);
-  for (int s = 0; s < 3; ++s)
-    for (int ps = 0; ps < kTile / 16; ++ps) {
-      const uint64_t ad = sdesc(zbuf + s * 256 * Kz + ps * 2 * Kz * 16, Kz * 16, 128);
-      const uint64_t bd = sdesc(xbuf + s * 256 * 16 + ps * 2 * 16 * 16, 16 * 16, 128);
-      mma_bf16(tW, ad, bd, id, (first && s == 0 && ps == 0) ? 0u : 1u);
+  auto part = [&](uint32_t tAcc, int k0, int k1, bool zero_first) {
+    for (int s = k0 >> 3; s <= (k1 - 1) >> 3; ++s) {
+      const int p0 = s == (k0 >> 3) ? (k0 & 7) : 0;
+      const int p1 = s == ((k1 - 1) >> 3) ? ((k1 - 1) & 7) + 1 : 8;
+      mma_chain(tAcc, sdesc(zbuf + s * 256 * Kz + p0 * 2 * Kz * 16, Kz * 16, 128), (2 * Kz * 16) >> 4,
+                sdesc(xbuf + s * 256 * 16 + p0 * 2 * 16 * 16, 256, 128), (2 * 16 * 16) >> 4, id, p1 - p0,
+                zero_first && s == (k0 >> 3));
     }
+  };
+  if (issuer == 3) part(tW, 0, split ? 12 : 24, first);
+  if (issuer == 2 && split) part(tP, 12, 24, true);
 }
 
 // ------------------------------------------------------------------ forward kernel
@@ -245,6 +333,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   constexpr int NG = HP / 16;
   extern __shared__ __align__(1024) uint8_t sm[];
   const TcPlan& pl = a.pl;
+  const TcTab* tb = tc_tab_init(pl, sm);       // read after the prologue barrier
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q4 = warp & 3, grp = warp >> 2;
   const int p = q4 * 32 + lane;                 // point (row / TMEM lane)
@@ -256,9 +345,10 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
   uint8_t* buf = sm + pl.o_buf[0];
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(bar, kIssuers);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const bool issuer = lane == 0 && warp < (int)kIssuers;   // issues and commits this CTA's MMAs
   // Tiles: the first from the CTA index, the later ones from the launch's
   // counter (the outputs of a tile do not depend on which CTA computes it),
   // requested two ahead so that the atomic and the next tile's coordinate
@@ -289,7 +379,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
     if (tid == 0) s_tl[(it + 1) & 1] = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);   // the tile after next
     float u = 0.f, ux = 0.f, uy = 0.f;          // output-layer partial sums over this thread's columns
     if (L == 2) {   // one hidden layer: output straight from layer 0
-      for (int o = c0; o < min(pl.w[1], c0 + 16); ++o) {
+      for (int o = c0; o < min(tb->w[1], c0 + 16); ++o) {
         const float wx = s_small[o], wy = s_small[HP + o];
         const float t = tanh_fast(fmaf(wx, x, fmaf(wy, y, s_small[2 * HP + o])));
         const float sd = fmaf(-t, t, 1.f), wl = s_small[3 * HP + o];
@@ -301,12 +391,13 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
       tc_fence_before();
       __syncthreads();
       for (int i = 1; i <= L - 2; ++i) {
-        const int Kin = pl.WP[i - 1], Nout = pl.WP[i];
-        if (tid == 0) {
+        const int Kin = tb->WP[i - 1], Nout = tb->WP[i];
+        if (issuer) {
           tc_fence_after();
-          issue_fwd(OP::fmt, tD, su32(buf), su32(sm + pl.o_w[i]), Kin, Nout, HP);
+          if (warp < 3) issue_fwd_stream(OP::fmt, tD, su32(buf), su32(sm + tb->o_w[i]), Kin, Nout, HP, warp);
           mma_commit(bar);
         }
+        __syncwarp();   // the issuer's warp-mates wait here, not in a polling loop beside it
         if (!mbar_wait(bar, phase)) {
           tfail = true;
           if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT);
@@ -314,7 +405,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
         phase ^= 1;
         tc_fence_after();
         const bool last = i == L - 2;
-        const int wo = pl.w[i + 1];
+        const int wo = tb->w[i + 1];
         // H_i also goes to the stash (same tile layout, streaming stores) when the
         // reverse sweep reads it: this thread's row and first column chunk of the
         // value stream
@@ -332,27 +423,39 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 3 : 2) mlp_fwd_tc
             tmem_ld8(tRow + 2 * HP + cc, dy);
             tmem_wait_ld();
             uint32_t pv[4], px[4], py[4];
+            if (last) {
+              // output layer: the bias column and the padding carry zero output
+              // weights, so no column needs patching here
+              const float4 wa = *reinterpret_cast<const float4*>(s_small + 3 * HP + cc);
+              const float4 wb = *reinterpret_cast<const float4*>(s_small + 3 * HP + cc + 4);
+              const float wl[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float t = tanh_fast(dv[j]);
+                const float sd = fmaf(-t, t, 1.f);
+                u = fmaf(wl[j], t, u);
+                ux = fmaf(wl[j] * sd, dx[j], ux);
+                uy = fmaf(wl[j] * sd, dy[j], uy);
+              }
+              continue;
+            }
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
               float tv[2], tx[2], ty[2];
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
-                const int o = cc + j + h;
                 const float t = tanh_fast(dv[j + h]);
                 const float sd = fmaf(-t, t, 1.f);
-                tv[h] = o == wo ? 1.f : t;
-                tx[h] = o == wo ? 0.f : sd * dx[j + h];
-                ty[h] = o == wo ? 0.f : sd * dy[j + h];
-                if (last) {
-                  const float wl = s_small[3 * HP + o];
-                  u = fmaf(wl, tv[h], u); ux = fmaf(wl, tx[h], ux); uy = fmaf(wl, ty[h], uy);
-                }
+                tv[h] = t;
+                tx[h] = sd * dx[j + h];
+                ty[h] = sd * dy[j + h];
               }
               pv[j >> 1] = OP::pack(tv[0], tv[1]);
               px[j >> 1] = OP::pack(tx[0], tx[1]);
               py[j >> 1] = OP::pack(ty[0], ty[1]);
             }
-            if (!last) {
+            if (wo >= cc && wo < cc + 8) set_bias_col<OP>(wo - cc, pv, px, py);
+            {
               // H_{i-1} (the MMA's A operand) is dead: overwrite the tile with H_i
               st8(buf, Nout, p, cc, pv);
               st8(buf + 256 * Nout, Nout, p, cc, px);
@@ -404,6 +507,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   constexpr int NT = tc_threads<HP>();
   extern __shared__ __align__(1024) uint8_t sm[];
   const TcPlan& pl = a.pl;
+  const TcTab* tb = tc_tab_init(pl, sm);       // read after the prologue barrier
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q4 = warp & 3, grp = warp >> 2;
   const int p = q4 * 32 + lane;                 // point (row / TMEM lane)
@@ -421,10 +525,11 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   auto stash_on = [&]() { return a.stash != nullptr && pl.n_stash > 0; };
   if (warp == 0) { tmem_alloc(s_tmem, pl.tmem_cols); tmem_relinquish(); }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(bar, kIssuers);
     if (stash_on()) mbar_init(ldbar, pl.n_stash);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the first tile's stashed layers, in flight under the weight prologue
+    // (before the barrier that publishes the shared table: kernel parameters here)
     if (stash_on() && blockIdx.x < (a.P_tot + kTile - 1) / kTile)
       for (int j = pl.stash_lo; j < pl.stash_lo + pl.n_stash; ++j) {
         const uint32_t bytes = 3u * 256u * (uint32_t)pl.WP[j];
@@ -459,10 +564,29 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   uint32_t phase = 0;
   bool failed = false;
   const int L = pl.L;
-  uint32_t wfirst = 0xFFFFFFFFu;   // bit i: Wbar_i accumulator not yet written (thread 0)
+  const bool issuer = lane == 0 && warp < (int)kIssuers;   // issues and commits this CTA's MMAs
+  constexpr int kWbarWarp = 3;     // the issuer of the weight-gradient chains (their first half when split)
+  const bool split = pl.c_part > 0;   // weight-gradient chains in two halves (a partial accumulator exists)
+  // Wbar_i += partial, this thread's lane quarter (rows in lanes 0..15) and column group
+  auto fold_part = [&](int i) {
+    const int ncols = i >= 1 ? tb->WP[i - 1] : 16;
+    for (int cb = c0; cb < c0 + 16 && cb < ncols; cb += 8) {
+      float pv[8], wv[8];
+      tmem_ld8(tRow + pl.c_part + cb, pv);
+      tmem_ld8(tRow + tb->c_wbar[i] + cb, wv);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) wv[j] += pv[j];
+      tmem_st8(tRow + tb->c_wbar[i] + cb, wv);
+    }
+    tmem_wait_st();
+  };
+  uint32_t wfirst = 0xFFFFFFFFu;   // bit i: Wbar_i accumulator not yet written (weight-gradient issuer)
   float accL[16];                  // output-layer weight gradient: this thread's columns, its points
 #pragma unroll
   for (int k = 0; k < 16; ++k) accL[k] = 0.f;
+  float accB = 0.f;                // output-bias gradient (the bias column's activation is 1): its points'
+                                   // value seeds, summed in tile order
   int bufH0 = -1, bufH1 = -1;      // layer held by activation tile 0 / 1
   const float sc = seed_scale(a.seed_absmax);   // adjoint scale (1 for BF16)
   const double inv_sc = 1.0 / (double)sc;
@@ -484,9 +608,9 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   auto stash_request = [&](int64_t t, int bufs) {
     for (int j = pl.stash_lo; j < pl.stash_lo + pl.n_stash; ++j) {
       if (!((bufs >> (j & 1)) & 1)) continue;
-      const uint32_t bytes = 3u * 256u * (uint32_t)pl.WP[j];
+      const uint32_t bytes = 3u * 256u * (uint32_t)tb->WP[j];
       mbar_expect_tx(ldbar, bytes);
-      bulk_load(sm + pl.o_buf[j & 1], a.stash + (t * pl.n_stash + (j - pl.stash_lo)) * (int64_t)pl.slot_bytes, bytes,
+      bulk_load(sm + tb->o_buf[j & 1], a.stash + (t * pl.n_stash + (j - pl.stash_lo)) * (int64_t)pl.slot_bytes, bytes,
                 ldbar, l2_evict_first());
     }
   };
@@ -498,15 +622,18 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     return __syncthreads_or(tfail) != 0;
   };
   auto issue_fwd_map = [&](int i) {
-    if (tid == 0) {
+    if (issuer) {
       tc_fence_after();
-      issue_fwd(OP::fmt, tD, su32(sm + pl.o_buf[(i - 1) & 1]), su32(sm + pl.o_w[i]), pl.WP[i - 1], pl.WP[i], HP);
+      if (warp < 3)
+        issue_fwd_stream(OP::fmt, tD, su32(sm + tb->o_buf[(i - 1) & 1]), su32(sm + tb->o_w[i]), tb->WP[i - 1], tb->WP[i],
+                         HP, warp);
       mma_commit(bar);
     }
+    __syncwarp();
   };
   // forward epilogue of hidden map i from D into activation tile `ob`
   auto fwd_epilogue_store = [&](int i, uint8_t* ob) {
-    const int Nout = pl.WP[i], wo = pl.w[i + 1];
+    const int Nout = tb->WP[i], wo = tb->w[i + 1];
     if (c0 >= Nout) return;
 #pragma unroll
     for (int sc8 = 0; sc8 < 16; sc8 += 8) {
@@ -522,17 +649,17 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         float tv[2], tx[2], ty[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int o = cc + j + h;
           const float t = tanh_fast(dv[j + h]);
           const float sd = fmaf(-t, t, 1.f);
-          tv[h] = o == wo ? 1.f : t;
-          tx[h] = o == wo ? 0.f : sd * dx[j + h];
-          ty[h] = o == wo ? 0.f : sd * dy[j + h];
+          tv[h] = t;
+          tx[h] = sd * dx[j + h];
+          ty[h] = sd * dy[j + h];
         }
         pv[j >> 1] = OP::pack(tv[0], tv[1]);
         px[j >> 1] = OP::pack(tx[0], tx[1]);
         py[j >> 1] = OP::pack(ty[0], ty[1]);
       }
+      if (wo >= cc && wo < cc + 8) set_bias_col<OP>(wo - cc, pv, px, py);
       st8(ob, Nout, p, cc, pv);
       st8(ob + 256 * Nout, Nout, p, cc, px);
       st8(ob + 512 * Nout, Nout, p, cc, py);
@@ -540,12 +667,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   };
   // recompute H_0 .. H_upto into the two activation tiles (H_j -> buf[j & 1])
   auto recompute = [&](int upto, float x, float y) -> bool {
-    layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+    layer0_store<OP>(pl, s_small, x, y, p, c0, sm + tb->o_buf[0]);
     if (publish()) return false;
     for (int j = 1; j <= upto; ++j) {
       issue_fwd_map(j);
       wait_mma();
-      fwd_epilogue_store(j, sm + pl.o_buf[j & 1]);
+      fwd_epilogue_store(j, sm + tb->o_buf[j & 1]);
       if (publish()) return false;
     }
     bufH0 = upto >= 1 ? ((upto & 1) == 0 ? upto : upto - 1) : 0;
@@ -561,6 +688,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
     const float x = (float)nxt.x, y = (float)nxt.y;
     const float su = sc * nxt.s[0], sx = sc * nxt.s[1], sy = sc * nxt.s[2];
+    accB += su;
     const bool has_next = tile + gridDim.x < n_tiles;
     if (has_next) point_fetch(a, (tile + gridDim.x) * kTile + p, nxt);
     if (grp == 0) {
@@ -574,7 +702,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
     const int last = L - 2;
     if (stash_on()) {
       // stored layers from the forward kernel; maps 1 .. last-1 are not recomputed
-      if (!stash_buf0() && !h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+      if (!stash_buf0() && !h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + tb->o_buf[0]);
       const bool ok = mbar_wait(ldbar, ldstate & 1u);
       ldstate = (ldstate & 1u) ^ 1u;
       if (__syncthreads_or(!ok)) { if (tid == 0) atomicExch(a.err, FV_ERR_TIMEOUT); failed = true; break; }
@@ -582,12 +710,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       issue_fwd_map(last);
       wait_mma();
     } else if (last >= 1) {
-      if (!h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+      if (!h0_ready) layer0_store<OP>(pl, s_small, x, y, p, c0, sm + tb->o_buf[0]);
       if (publish()) { failed = true; break; }
       for (int i = 1; i < last; ++i) {
         issue_fwd_map(i);
         wait_mma();
-        fwd_epilogue_store(i, sm + pl.o_buf[i & 1]);
+        fwd_epilogue_store(i, sm + tb->o_buf[i & 1]);
         if (publish()) { failed = true; break; }
       }
       if (failed) break;
@@ -595,7 +723,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       wait_mma();
     }
     {
-      const int Nout = pl.WP[last], wo = pl.w[last + 1];
+      const int Nout = tb->WP[last], wo = tb->w[last + 1];
       if (c0 < Nout) {
 #pragma unroll
         for (int sc8 = 0; sc8 < 16; sc8 += 8) {
@@ -622,11 +750,13 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
             float zv[2], zx[2], zy[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+              // the bias column (o == wo) has zero weights into it and a zero output
+              // weight: its t, tangents and adjoints come out 0 here; only the
+              // output-bias gradient needs its value 1, added below
               const int o = cc + j + h;
-              float t = tanh_fast(dv[j + h]);
-              float sd = fmaf(-t, t, 1.f);
-              float tx = sd * dx[j + h], ty = sd * dy[j + h];
-              if (o == wo) { t = 1.f; tx = 0.f; ty = 0.f; sd = 0.f; }
+              const float t = tanh_fast(dv[j + h]);
+              const float sd = fmaf(-t, t, 1.f);
+              const float tx = sd * dx[j + h], ty = sd * dy[j + h];
               float& acc = accL[sc8 + j + h];
               acc = fmaf(su, t, fmaf(sx, tx, fmaf(sy, ty, acc)));
               const float wl = s_small[3 * HP + o];
@@ -658,21 +788,25 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         if ((((i - 1) & 1) ? bufH1 : bufH0) != i - 1) {
           if (!recompute(i - 1, x, y)) { failed = true; break; }
         }
-        bsrc = su32(sm + pl.o_buf[(i - 1) & 1]);
-        Kb = pl.WP[i - 1];
+        bsrc = su32(sm + tb->o_buf[(i - 1) & 1]);
+        Kb = tb->WP[i - 1];
       } else {
         bsrc = su32(xbuf);
         Kb = 16;
       }
-      if (tid == 0) {
+      if (issuer) {
         tc_fence_after();
         if (i >= 1)
-          issue_reverse(OP::fmt, tD, tD + pl.c_wbar[i], su32(zb), su32(sm + pl.o_w[i]), bsrc, pl.WP[i - 1], pl.WP[i],
-                        HP, (wfirst >> i) & 1u);
+          issue_reverse(OP::fmt, tD, tD + tb->c_wbar[i], tD + pl.c_part, split, su32(zb), su32(sm + tb->o_w[i]), bsrc,
+                        tb->WP[i - 1], tb->WP[i], HP, (wfirst >> i) & 1u, warp);
         else
-          issue_wbar0(OP::fmt, tD + pl.c_wbar[0], su32(zb), pl.WP[0], bsrc, (wfirst >> 0) & 1u);
+          issue_wbar0(OP::fmt, tD + tb->c_wbar[0], tD + pl.c_part, split, su32(zb), tb->WP[0], bsrc, (wfirst >> 0) & 1u,
+                      warp);
         wfirst &= ~(1u << i);
         mma_commit(bar);
+      }
+      __syncwarp();
+      if (tid == 0) {
         // the next tile's stashed layers into buffers this tile no longer reads:
         // buf[1] from step 1 on (only H_0 in buf[0] is left), buf[0] at step 0
         if (stash_on() && has_next && i <= 1) {
@@ -686,18 +820,19 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       // and under map 0's step the next tile's H_0 (buf[0] held this tile's H_0,
       // read by map 1's step only)
       if (i == 2 && bufH0 != 0) {
-        layer0_store<OP>(pl, s_small, x, y, p, c0, sm + pl.o_buf[0]);
+        layer0_store<OP>(pl, s_small, x, y, p, c0, sm + tb->o_buf[0]);
         bufH0 = 0;
       }
       if (i == 0) {
         h0_ready = last >= 1 && has_next && !stash_buf0();
-        if (h0_ready) layer0_store<OP>(pl, s_small, (float)nxt.x, (float)nxt.y, p, c0, sm + pl.o_buf[0]);
+        if (h0_ready) layer0_store<OP>(pl, s_small, (float)nxt.x, (float)nxt.y, p, c0, sm + tb->o_buf[0]);
       }
       wait_mma();
+      if (split) fold_part(i);
       if (i >= 1) {
         // Zbar_{i-1} from Tbar_{i-1} (tensor memory) and H_{i-1} (shared tile), tanh rule
-        const int K = pl.WP[i - 1];
-        const uint8_t* hb = sm + pl.o_buf[(i - 1) & 1];
+        const int K = tb->WP[i - 1];
+        const uint8_t* hb = sm + tb->o_buf[(i - 1) & 1];
         if (c0 < K) {
 #pragma unroll
           for (int sc8 = 0; sc8 < 16; sc8 += 8) {
@@ -740,7 +875,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   if (ldstate & 2u) mbar_wait(ldbar, ldstate & 1u);   // after a failure: let requested copies land
   // ---- write this CTA's gradient partials
   uint32_t* s_flags = reinterpret_cast<uint32_t*>(sm + pl.o_bar + 12);
-  if (tid == 0) *s_flags = wfirst;          // accumulators never written by this CTA
+  if (tid == kWbarWarp * 32) *s_flags = wfirst;   // accumulators never written by this CTA
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -751,12 +886,12 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       // hidden maps 0..L-2 from tensor memory (M = 64 layout: row o in lane (o/16)*32 + o%16)
       const int o = q4 * 16 + lane;
       for (int i = 0; i <= L - 2; ++i) {
-        const int Kb = i >= 1 ? pl.WP[i - 1] : 16;
-        const int in = pl.w[i], out = pl.w[i + 1];
+        const int Kb = i >= 1 ? tb->WP[i - 1] : 16;
+        const int in = tb->w[i], out = tb->w[i + 1];
         const bool never = (never_mask >> i) & 1u;
         for (int cb = 0; cb < Kb; cb += 8) {
           float v[8];
-          tmem_ld8(tRow + pl.c_wbar[i] + cb, v);
+          tmem_ld8(tRow + tb->c_wbar[i] + cb, v);
           tmem_wait_ld();
 
           if (lane < 16 && o < out) {
@@ -764,8 +899,8 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
             for (int j = 0; j < 8; ++j) {
               const int k = cb + j;
               const double val = never ? 0.0 : (double)v[j] * inv_sc;
-              if (k < in) g[pl.off[i] + o * in + k] = val;
-              else if (k == in) g[pl.off[i] + out * in + o] = val;
+              if (k < in) g[tb->off[i] + o * in + k] = val;
+              else if (k == in) g[tb->off[i] + out * in + o] = val;
             }
           }
         }
@@ -777,15 +912,15 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
   // output layer: reduce accL over the CTA's 128 points in fixed order
   tc_fence_before();
   __syncthreads();
-  float* scratch = reinterpret_cast<float*>(sm + pl.o_buf[0]);   // [128][HP]
+  float* scratch = reinterpret_cast<float*>(sm + tb->o_buf[0]);   // [128][HP]
+  const int win = tb->w[L - 1];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) scratch[p * HP + c0 + k] = accL[k];
+  for (int k = 0; k < 16; ++k) scratch[p * HP + c0 + k] = c0 + k == win ? accB : accL[k];
   __syncthreads();
   if (tid < HP) {
     double sum = 0.0;
     for (int t = 0; t < kTile; ++t) sum += (double)scratch[t * HP + tid];
-    const int win = pl.w[L - 1];
-    if (tid <= win) g[pl.off[L - 1] + tid] = failed ? 0.0 : sum * inv_sc;
+    if (tid <= win) g[tb->off[L - 1] + tid] = failed ? 0.0 : sum * inv_sc;
   }
   tc_fence_before();
   __syncthreads();
@@ -831,14 +966,24 @@ bool make_tc_plan(const EvalPlan& ep, bool reverse, TcPlan* p) {
   }
   p->o_red = o; o += kTile * (HP / 16) * 3 * 4;
   p->o_bar = o; o += 48;
+  p->o_tab = o; o += (int)sizeof(TcTab);
   p->smem = (o + 127) & ~127;
   int cols = 3 * HP;
   if (reverse) {
     for (int i = 1; i <= s.L - 2; ++i) { p->c_wbar[i] = cols; cols += HP; }
     p->c_wbar[0] = cols; cols += 16;
   }
-  int t = 32;
-  while (t < cols) t *= 2;
+  auto alloc_cols = [](int c) { int t = 32; while (t < c) t *= 2; return t; };
+  int t = alloc_cols(cols);
+  // reverse: a partial weight-gradient accumulator (HP columns) splits each
+  // weight-gradient chain in two; taken where it keeps the allocation (and the
+  // CTAs per SM) unchanged
+  p->c_part = 0;
+  if (reverse && alloc_cols(cols + HP) == t) {
+    p->c_part = cols;
+    cols += HP;
+    t = alloc_cols(cols);
+  }
   if (t > 512) return false;
   p->tmem_cols = t;
   const int last = s.L - 2;

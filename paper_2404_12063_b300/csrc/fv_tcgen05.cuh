@@ -13,16 +13,15 @@
 namespace fv {
 namespace tc {
 
-constexpr uint64_t kTcWaitNs = 2000000000ull;   // every mbarrier wait gives up after 2 s
+// every mbarrier wait gives up after 4e9 SM cycles (2 s at the 2032 MHz maximum
+// clock, longer at lower clocks); the bound is kept in SM cycles because the
+// cycle counter is cheap to read, while a read of the global nanosecond timer
+// costs hundreds of cycles
+constexpr long long kTcWaitCycles = 4000000000ll;
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
@@ -42,18 +41,28 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// One test of the phase; a thread whose phase is not complete is suspended
+// until it completes or for at most about 1 ms (the suspend-time hint), so
+// waiting threads leave the issue slots to the threads they wait for (the MMA
+// issuers share the SM sub-partitions with them).
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (gtimer() - t0 > kTcWaitNs) return false;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity), "n"(1000000)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with parity `parity` to complete; false after the bound.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kTcWaitCycles) return false;
   }
+  return true;
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -113,6 +122,8 @@ __device__ __forceinline__ uint32_t idesc_f16(uint32_t fmt, int M, int N, int a_
 // power of two to stay inside FP16's range).
 struct OpBF16 {
   static constexpr uint32_t fmt = 1;
+  static constexpr uint32_t one = 0x3F80u;   // 1.0
+
   __device__ static __forceinline__ uint32_t pack(float lo, float hi) {
     uint32_t r;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
@@ -123,6 +134,8 @@ struct OpBF16 {
 };
 struct OpF16 {
   static constexpr uint32_t fmt = 0;
+  static constexpr uint32_t one = 0x3C00u;   // 1.0
+
   __device__ static __forceinline__ uint32_t pack(float lo, float hi) {
     uint32_t r;
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
@@ -136,6 +149,23 @@ __device__ __forceinline__ float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// The bias column of an activation tile holds (1, 0, 0) in the value and
+// tangent streams.  Of eight packed columns [cc, cc + 8) (four words per
+// stream), set column k to that: value 1, tangents 0.  Called only by the
+// warps whose column range holds the bias column (a warp-uniform branch).
+template <class OP>
+__device__ __forceinline__ void set_bias_col(int k, uint32_t pv[4], uint32_t px[4], uint32_t py[4]) {
+  const int sel = k >> 1;
+  const uint32_t keep = (k & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+  const uint32_t one = (k & 1) ? (OP::one << 16) : OP::one;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {           // constant indices: the words stay in registers
+    pv[w] = sel == w ? ((pv[w] & keep) | one) : pv[w];
+    px[w] = sel == w ? (px[w] & keep) : px[w];
+    py[w] = sel == w ? (py[w] & keep) : py[w];
+  }
 }
 
 // Activation tile layout (one stream): row p, column k of a [128 x Kb] BF16

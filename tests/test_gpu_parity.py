@@ -559,6 +559,46 @@ def test_batch_tensor_core_vs_individual_calls(api, ctx, n_streams):
             assert rel(g.cpu().double().numpy(), g2.cpu().double().numpy()) < 1e-5
 
 
+@functools.lru_cache(maxsize=None)
+def batch64():
+    """Config 5: 64 uneven Poisson instances, and the oracle's result for each.
+    Both GPU forms below run the network with FP32 parameters, so the oracle
+    sees those (rounded) values; R is kept for the element-wise check."""
+    probs = fi.poisson_batch(64)
+    p32 = [np.asarray(p.params, dtype=np.float32).astype(np.float64) for p in probs]
+    refs = [oracle_eval(p, q, want_R=True) for p, q in zip(probs, p32)]
+    return probs, refs
+
+
+@pytest.mark.parametrize("precision,storage", [("fp32", "fp32"), ("fp16", "bf16")])
+def test_batch_64_instances_against_oracle(api, ctx, precision, storage):
+    """The whole 64-instance batch (N_e from 100 to 15,376, Q = 5..10, T = 4..8:
+    26 (Q, T) pairs and both tensor-core tile widths' contraction plans) in one
+    graph launch with the autotuned stream count: every instance's loss parts
+    and gradient against the oracle, and R element by element for one instance
+    of every (Q, T) pair drawn (Alg. 3 applied per instance)."""
+    probs, refs = batch64()
+    pbs = [api.problem_from_inputs(ctx, p, precision, storage=storage) for p in probs]
+    params = [torch.tensor(p.params, dtype=pb.dtype, device="cuda") for p, pb in zip(probs, pbs)]
+    batch = api.Batch(ctx, pbs, params, n_streams=0)
+    outs, grads = batch.run()
+    torch.cuda.synchronize()
+    tol = TOL[precision]
+    for i, (o, g, ref) in enumerate(zip(outs, grads, refs)):
+        o = o.cpu().numpy()
+        assert rel(o[0], ref["loss"]) < tol, (i, o[0], ref["loss"])
+        assert rel(o[1], ref["Lv"]) < tol, (i, o[1], ref["Lv"])
+        assert rel(o[2], ref["Lb"]) < tol, (i, o[2], ref["Lb"])
+        assert rel(g.cpu().double().numpy(), ref["grad"]) < tol, i
+    first = {}
+    for i, p in enumerate(probs):
+        first.setdefault((p.quad_order, p.test_order), i)
+    assert len(first) >= 20
+    for (Q, T), i in sorted(first.items()):
+        _, _, _, R = pbs[i].intermediates(params[i])
+        assert rel(R.cpu().numpy(), refs[i]["R"]) < tol, (Q, T, i)
+
+
 def test_kernel_timing_records(api, ctx):
     prob = cfg("tiny")
     pb = api.problem_from_inputs(ctx, prob, "fp32")
