@@ -124,7 +124,7 @@ CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "s
 
 class ClockSampler:
     """SM clock, its maximum, board power and the throttle reasons, sampled
-    every 20 ms from a thread while the GPU is under load (NVML reads only;
+    every 5 ms from a thread while the GPU is under load (NVML reads only;
     nothing is set).  Falls back to a line-buffered nvidia-smi loop with the
     query fields this driver accepts."""
 
@@ -135,37 +135,44 @@ class ClockSampler:
         self.proc = None
         self.stop_flag = False
 
-    def _nvml_handle(self):
-        import pynvml
-        pynvml.nvmlInit()
+    def _nvml(self):
+        """NVML through ctypes (libnvidia-ml.so.1; read-only queries), the device
+        matched to the CUDA device by PCI bus id."""
+        import ctypes as C
+        nv = C.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = C.c_void_p()
         try:
             import torch
             pr = torch.cuda.get_device_properties(self.cuda_index)
-            bus = "%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), pr.pci_bus_id, pr.pci_device_id)
-            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+            bus = ("%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), pr.pci_bus_id, pr.pci_device_id)).encode()
+            if nv.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) != 0:
+                raise RuntimeError("no device for bus id")
         except Exception:
-            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.cuda_index)
+            if nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.cuda_index), C.byref(h)) != 0:
+                raise RuntimeError("no NVML device")
+        return nv, h
 
     def _nvml_loop(self, nv, h):
-        bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
-                "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
-                "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
-                "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
-        mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+        import ctypes as C
+        bits = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+        reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx, sm, pw, rs = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))          # 1: the SM clock
         while not self.stop_flag:
-            try:
-                sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
-                pw = nv.nvmlDeviceGetPowerUsage(h) / 1e3
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.samples.append((sm, mx, pw, [n for n, b in bits.items() if r & b]))
-            except Exception:
-                pass
-            time.sleep(0.02)
+            if nv.nvmlDeviceGetClockInfo(h, 1, C.byref(sm)) == 0:
+                nv.nvmlDeviceGetPowerUsage(h, C.byref(pw))
+                reasons_fn(h, C.byref(rs))
+                self.samples.append((float(sm.value), float(mx.value), pw.value / 1e3,
+                                     [n for n, b in bits.items() if rs.value & b]))
+            time.sleep(0.005)
 
     def start(self):
         import threading
         try:
-            nv, h = self._nvml_handle()
+            nv, h = self._nvml()
             self.kind = "nvml"
             self.thread = threading.Thread(target=self._nvml_loop, args=(nv, h), daemon=True)
             self.thread.start()

@@ -809,6 +809,8 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       if (tid == 0) {
         // the next tile's stashed layers into buffers this tile no longer reads:
         // buf[1] from step 1 on (only H_0 in buf[0] is left), buf[0] at step 0
+        // (requesting buf[0] once step 1's MMAs are done, with epilogue 1
+        // recomputing H_0, measured slower: 494 against 451 us)
         if (stash_on() && has_next && i <= 1) {
           fence_proxy_async();
           stash_request(tile + gridDim.x, i == 1 ? 2 : 1);
@@ -833,7 +835,49 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
         // Zbar_{i-1} from Tbar_{i-1} (tensor memory) and H_{i-1} (shared tile), tanh rule
         const int K = tb->WP[i - 1];
         const uint8_t* hb = sm + tb->o_buf[(i - 1) & 1];
-        if (c0 < K) {
+        // this thread's 8 columns [cc, cc + 8) of H_{i-1}, 3 streams, as stored (16-bit pairs)
+        auto h_packed = [&](int cc, uint32_t hv[4], uint32_t hx[4], uint32_t hy[4]) {
+          const uint32_t ho = row_off(p, K) + (cc >> 3) * 128;
+          const uint4 Hv = *reinterpret_cast<const uint4*>(hb + ho);
+          const uint4 Hx = *reinterpret_cast<const uint4*>(hb + 256 * K + ho);
+          const uint4 Hy = *reinterpret_cast<const uint4*>(hb + 512 * K + ho);
+          hv[0] = Hv.x; hv[1] = Hv.y; hv[2] = Hv.z; hv[3] = Hv.w;
+          hx[0] = Hx.x; hx[1] = Hx.y; hx[2] = Hx.z; hx[3] = Hx.w;
+          hy[0] = Hy.x; hy[1] = Hy.y; hy[2] = Hy.z; hy[3] = Hy.w;
+        };
+        if (c0 < K && OP::fmt == OpF16::fmt) {
+          // FP16: the tanh rule in packed half2 arithmetic on the FP16 activations as
+          // stored (two columns per instruction); the adjoints from tensor memory are
+          // rounded to FP16 first (they are stored in FP16 anyway)
+#pragma unroll
+          for (int sc8 = 0; sc8 < 16; sc8 += 8) {
+            const int cc = c0 + sc8;
+            float bv[8], bx[8], by[8];
+            tmem_ld8(tRow + cc, bv);
+            tmem_ld8(tRow + HP + cc, bx);
+            tmem_ld8(tRow + 2 * HP + cc, by);
+            uint32_t hv[4], hx[4], hy[4];
+            h_packed(cc, hv, hx, hy);
+            tmem_wait_ld();
+            uint32_t pv[4], px[4], py[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              const __half2 one = __float2half2_rn(1.f);
+              const __half2 t = u32_h2(hv[w]), tx = u32_h2(hx[w]), ty = u32_h2(hy[w]);
+              const __half2 gv = __floats2half2_rn(bv[2 * w], bv[2 * w + 1]);
+              const __half2 gx = __floats2half2_rn(bx[2 * w], bx[2 * w + 1]);
+              const __half2 gy = __floats2half2_rn(by[2 * w], by[2 * w + 1]);
+              const __half2 sd = __hfma2(__hneg2(t), t, one);
+              const __half2 q = __hfma2(ty, gy, __hmul2(tx, gx));
+              pv[w] = h2_u32(__hfma2(sd, gv, __hneg2(__hmul2(__hadd2(t, t), q))));
+              px[w] = h2_u32(__hmul2(sd, gx));
+              py[w] = h2_u32(__hmul2(sd, gy));
+            }
+            st8(zb, K, p, cc, pv);
+            st8(zb + 256 * K, K, p, cc, px);
+            st8(zb + 512 * K, K, p, cc, py);
+          }
+        } else if (c0 < K) {
 #pragma unroll
           for (int sc8 = 0; sc8 < 16; sc8 += 8) {
             const int cc = c0 + sc8;
@@ -841,9 +885,16 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
             tmem_ld8(tRow + cc, bv);
             tmem_ld8(tRow + HP + cc, bx);
             tmem_ld8(tRow + 2 * HP + cc, by);
-            ld8<OP>(hb, K, p, cc, hv);
-            ld8<OP>(hb + 256 * K, K, p, cc, hx);
-            ld8<OP>(hb + 512 * K, K, p, cc, hy);
+            {
+              uint32_t uv[4], ux[4], uy[4];
+              h_packed(cc, uv, ux, uy);
+#pragma unroll
+              for (int w = 0; w < 4; ++w) {
+                hv[2 * w] = OP::lo(uv[w]); hv[2 * w + 1] = OP::hi(uv[w]);
+                hx[2 * w] = OP::lo(ux[w]); hx[2 * w + 1] = OP::hi(ux[w]);
+                hy[2 * w] = OP::lo(uy[w]); hy[2 * w + 1] = OP::hi(uy[w]);
+              }
+            }
             tmem_wait_ld();
             uint32_t pv[4], px[4], py[4];
 #pragma unroll

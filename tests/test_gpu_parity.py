@@ -185,6 +185,26 @@ def test_inverse_full(api, ctx, precision):
     check_against_oracle(api, ctx, cfg("inverse"), precision)
 
 
+@pytest.mark.parametrize("n,Q,T", [(2, 20, 5), (8, 10, 5), (32, 5, 5)])
+@pytest.mark.parametrize("eps", [2.0, 0.7, 0.3])
+def test_fp16_dL_deps_alone(api, ctx, n, Q, T, eps):
+    """dL/deps of the FP16 tensor-core form (FP32 G) on its own against the
+    oracle, at 2e-2, on the inverse problem (Sec. 4.7.1) at the start network and
+    three eps: on 2 x 2 elements with 20 x 20 quadrature points (close to the
+    paper's own inverse setting), 8 x 8 elements at Q = 10, and 32 x 32 at the
+    config's Q = 5.  dL/deps = (2/N_t) sum R A with A = the eps coefficient of the
+    residual, a quadrature sum of grad u . grad v over an element that cancels to
+    O(h^2) of its terms (for linear u it is 0 exactly, the patch test): 16-bit
+    noise in grad u does not cancel with it, so the error of this one coordinate
+    grows like 1/h and with G's rounding; on the full 256 x 256 mesh it is no
+    longer within 2e-2 (measured values are recorded with the design notes)."""
+    prob = _with(fi.inverse_cd2d(n), quad_order=Q, test_order=T, eps=eps)
+    pb, params, out, grad = gpu_eval(api, ctx, prob, "fp16", storage="fp32")
+    ref = oracle_eval(prob, params.cpu().double().numpy())
+    assert rel(out[4], ref["dL_deps"]) < 2e-2, (out[4], ref["dL_deps"])
+    assert rel(grad, ref["grad"]) < 2e-2
+
+
 def test_inverse_gradient_vs_central_differences(api, ctx):
     """GPU FP64 gradient against central differences of GPU FP64 losses, on a
     random subset of coordinates plus eps (inverse-problem mesh, 32x32)."""
