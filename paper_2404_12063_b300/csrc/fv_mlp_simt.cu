@@ -29,7 +29,8 @@
 namespace fv {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;      // forward kernel
+constexpr int kThreadsBwd = 512;   // reverse kernel: its shared memory allows one CTA per SM, so 16 warps
 
 struct WLayout {
   int woff[kMaxLayers];  // padded W_i: rows ru4(out) x ld ru4(in), row-major
@@ -70,6 +71,7 @@ struct FwdArgs {
   MlpShape sh;
   WLayout wl;
   int DP, TP, TPS;
+  int inplace;   // one activation buffer (every micro-tile is one thread's)
   const void* params;
   const double* Xm;
   int64_t P_mesh;
@@ -82,6 +84,8 @@ struct BwdArgs {
   MlpShape sh;
   WLayout wl;
   int DP, TP, TPS;
+  int pp;        // points per micro-tile of the forward and adjoint GEMMs (4, 2 or 1: small point tiles)
+  int wsplit;    // threads sharing one weight-gradient micro-tile (1 or 2)
   const void* params;
   const double* Xm;
   int64_t P_mesh;
@@ -107,31 +111,40 @@ __device__ __forceinline__ void st4(double* p, const double v[4]) {
   *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
 }
+__device__ __forceinline__ void ld2(const float* p, float v[2]) {
+  const float2 t = *reinterpret_cast<const float2*>(p);
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void ld2(const double* p, double v[2]) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void st2(float* p, const float v[2]) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+__device__ __forceinline__ void st2(double* p, const double v[2]) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
+// PP (4 or 2) consecutive values
+template <int PP, class R> __device__ __forceinline__ void ldp(const R* p, R v[PP]) {
+  if constexpr (PP == 4) ld4(p, v);
+  else if constexpr (PP == 2) ld2(p, v);
+  else v[0] = p[0];
+}
+template <int PP, class R> __device__ __forceinline__ void stp(R* p, const R v[PP]) {
+  if constexpr (PP == 4) st4(p, v);
+  else if constexpr (PP == 2) st2(p, v);
+  else p[0] = v[0];
+}
 __device__ __forceinline__ float tanh_r(float v) { return tanhf(v); }
 __device__ __forceinline__ double tanh_r(double v) { return tanh(v); }
 
-// Per-CTA weight-gradient accumulator in shared memory: FP64 on the FP64
-// path; on the FP32 path a compensated (Kahan) FP32 pair per entry, which
-// keeps FP64 arithmetic (slow on this part) out of the tile loop.
-template <class R> struct GradAcc;
-template <> struct GradAcc<double> {
-  double* a;
-  __device__ __forceinline__ void zero(int i) { a[i] = 0.0; }
-  __device__ __forceinline__ void add(int i, double v) { a[i] += v; }
-  __device__ __forceinline__ double get(int i) const { return a[i]; }
-};
-template <> struct GradAcc<float> {
-  float2* a;   // (sum, compensation)
-  __device__ __forceinline__ void zero(int i) { a[i] = make_float2(0.f, 0.f); }
-  __device__ __forceinline__ void add(int i, float v) {
-    float2 t = a[i];
-    const float y = v - t.y;
-    const float u = t.x + y;
-    t.y = (u - t.x) - y;
-    t.x = u;
-    a[i] = t;
-  }
-  __device__ __forceinline__ double get(int i) const { return (double)a[i].x - (double)a[i].y; }
+// Per-CTA weight-gradient accumulator in shared memory, one entry per
+// parameter in the path's precision: a tile's contribution is formed in
+// registers over its 3 x TP point-streams and added once per tile, and the
+// per-CTA partials are summed in FP64 across CTAs.  (A compensated FP32 pair
+// per entry took twice the shared memory, and with it half the tile size.)
+template <class R> struct GradAcc {
+  R* a;
+  __device__ __forceinline__ void zero(int i) { a[i] = (R)0; }
+  __device__ __forceinline__ void add(int i, R v) { a[i] += v; }
+  __device__ __forceinline__ double get(int i) const { return (double)a[i]; }
 };
 
 // Load the padded weights into shared memory (zero padding).
@@ -176,20 +189,72 @@ __device__ void fwd_layer0(const R* W, const R* b, int ld, int rows, const R* sX
   }
 }
 
-// Hidden layer: B = tanh-rule(W A + b) for the three streams; 4x4 (o, p) micro-tiles.
-template <class R>
+// Hidden layer: B = tanh-rule(W A + b) for the three streams; 4 x PP (o, p)
+// micro-tiles (PP = 2 or 1 multiplies the micro-tiles of a small point tile).
+template <class R, int PP = 4>
 __device__ void fwd_layer(const R* __restrict__ W, const R* __restrict__ b, int ld, int in, int rows,
                           const R* __restrict__ A, R* __restrict__ B, int TP, int TPS, int plane) {
-  const int n_pg = TP >> 2, n_og = rows >> 2;
+  const int n_pg = TP / PP, n_og = rows >> 2;
   for (int mt = threadIdx.x; mt < n_og * n_pg; mt += blockDim.x) {
-    const int pg = mt % n_pg, og = mt / n_pg, p0 = pg << 2;
-    R acc[3][4][4];
+    const int pg = mt % n_pg, og = mt / n_pg, p0 = pg * PP;
+    R acc[3][4][PP];
 #pragma unroll
     for (int s = 0; s < 3; ++s)
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[s][i][j] = (R)0;
+        for (int j = 0; j < PP; ++j) acc[s][i][j] = (R)0;
+    for (int k = 0; k < in; ++k) {
+      R a0[PP], a1[PP], a2[PP], w[4];
+      ldp<PP>(A + k * TPS + p0, a0);
+      ldp<PP>(A + plane + k * TPS + p0, a1);
+      ldp<PP>(A + 2 * plane + k * TPS + p0, a2);
+#pragma unroll
+      for (int oo = 0; oo < 4; ++oo) w[oo] = W[(og + oo * n_og) * ld + k];
+#pragma unroll
+      for (int oo = 0; oo < 4; ++oo)
+#pragma unroll
+        for (int pp = 0; pp < PP; ++pp) {
+          acc[0][oo][pp] = fma(w[oo], a0[pp], acc[0][oo][pp]);
+          acc[1][oo][pp] = fma(w[oo], a1[pp], acc[1][oo][pp]);
+          acc[2][oo][pp] = fma(w[oo], a2[pp], acc[2][oo][pp]);
+        }
+    }
+#pragma unroll
+    for (int oo = 0; oo < 4; ++oo) {
+      const int o = og + oo * n_og;
+      const R bo = b[o];
+      R t4[PP], x4[PP], y4[PP];
+#pragma unroll
+      for (int pp = 0; pp < PP; ++pp) {
+        const R t = tanh_r(acc[0][oo][pp] + bo), s = (R)1 - t * t;
+        t4[pp] = t; x4[pp] = s * acc[1][oo][pp]; y4[pp] = s * acc[2][oo][pp];
+      }
+      stp<PP>(B + o * TPS + p0, t4);
+      stp<PP>(B + plane + o * TPS + p0, x4);
+      stp<PP>(B + 2 * plane + o * TPS + p0, y4);
+    }
+  }
+}
+
+// Hidden layer in place: every micro-tile of the CTA is one thread's (the
+// caller checks rows/4 x TP/4 <= blockDim), so each thread holds its results
+// in registers across a barrier and then overwrites A with B.
+template <class R>
+__device__ void fwd_layer_inplace(const R* __restrict__ W, const R* __restrict__ b, int ld, int in, int rows, R* A,
+                                  int TP, int TPS, int plane) {
+  const int n_pg = TP >> 2, n_og = rows >> 2;
+  const int mt = threadIdx.x;
+  const bool active = mt < n_og * n_pg;
+  const int pg = active ? mt % n_pg : 0, og = active ? mt / n_pg : 0, p0 = pg << 2;
+  R acc[3][4][4];
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[s][i][j] = (R)0;
+  if (active) {
     for (int k = 0; k < in; ++k) {
       R a0[4], a1[4], a2[4], w[4];
       ld4(A + k * TPS + p0, a0);
@@ -206,6 +271,9 @@ __device__ void fwd_layer(const R* __restrict__ W, const R* __restrict__ b, int 
           acc[2][oo][pp] = fma(w[oo], a2[pp], acc[2][oo][pp]);
         }
     }
+  }
+  __syncthreads();
+  if (active) {
 #pragma unroll
     for (int oo = 0; oo < 4; ++oo) {
       const int o = og + oo * n_og;
@@ -216,21 +284,23 @@ __device__ void fwd_layer(const R* __restrict__ W, const R* __restrict__ b, int 
         const R t = tanh_r(acc[0][oo][pp] + bo), s = (R)1 - t * t;
         t4[pp] = t; x4[pp] = s * acc[1][oo][pp]; y4[pp] = s * acc[2][oo][pp];
       }
-      st4(B + o * TPS + p0, t4);
-      st4(B + plane + o * TPS + p0, x4);
-      st4(B + 2 * plane + o * TPS + p0, y4);
+      st4(A + o * TPS + p0, t4);
+      st4(A + plane + o * TPS + p0, x4);
+      st4(A + 2 * plane + o * TPS + p0, y4);
     }
   }
 }
 
 // ----------------------------------------------------------------------------- forward kernel
+// inplace: one activation buffer, updated layer by layer (fwd_layer_inplace);
+// otherwise two, alternating.
 template <class R>
 __global__ void __launch_bounds__(kThreads) mlp_fwd_simt(FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   R* sW = reinterpret_cast<R*>(smem);
   const int plane = a.DP * a.TPS;
   R* bufA = sW + a.wl.total;
-  R* bufB = bufA + 3 * plane;
+  R* bufB = a.inplace ? bufA : bufA + 3 * plane;
   R* sX = bufB + 3 * plane;
   const MlpShape& sh = a.sh;
   const WLayout& wl = a.wl;
@@ -248,9 +318,14 @@ __global__ void __launch_bounds__(kThreads) mlp_fwd_simt(FwdArgs a) {
     fwd_layer0<R>(sW + wl.woff[0], sW + wl.boff[0], wl.ld[0], wl.rows[0], sX, A, a.TP, a.TPS, plane);
     __syncthreads();
     for (int i = 1; i < L - 1; ++i) {
-      fwd_layer<R>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i], A, B, a.TP, a.TPS, plane);
-      __syncthreads();
-      R* t = A; A = B; B = t;
+      if (a.inplace) {
+        fwd_layer_inplace<R>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i], A, a.TP, a.TPS, plane);
+        __syncthreads();
+      } else {
+        fwd_layer<R>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i], A, B, a.TP, a.TPS, plane);
+        __syncthreads();
+        R* t = A; A = B; B = t;
+      }
     }
     const R* Wl = sW + wl.woff[L - 1];
     const R bl = sW[wl.boff[L - 1]];
@@ -295,22 +370,34 @@ __device__ void bwd_elementwise(const R* __restrict__ S, const R* __restrict__ T
 }
 
 // gW[o][k] += sum_s sum_p Zb[s][o][p] H[s][k][p]; 4x4 (o, k) micro-tiles with
-// interleaved rows (o = og + n_og*oo, k = kg + n_kg*kk).
+// interleaved rows (o = og + n_og*oo, k = kg + n_kg*kk).  With split = 2 each
+// micro-tile's sum over the 3 x TP point-streams is shared by two threads (the
+// first and second halves of the 4-point steps); the second leaves its part in
+// `scratch` ([micro-tile][16]) and the first adds it, then its own sum goes to
+// the accumulator: a fixed order.  Every thread of the CTA takes part (barrier).
 template <class R>
 __device__ void wgrad_layer(const R* __restrict__ Zb, const R* __restrict__ H, int out, int in, int rows_o,
-                            int rows_k, int TP, int TPS, int plane, GradAcc<R> G, int off) {
-  const int n_og = rows_o >> 2, n_kg = rows_k >> 2;
-  for (int mt = threadIdx.x; mt < n_og * n_kg; mt += blockDim.x) {
-    const int kg = mt % n_kg, og = mt / n_kg;
+                            int rows_k, int TP, int TPS, int plane, GradAcc<R> G, int off, int split,
+                            R* __restrict__ scratch) {
+  const int n_og = rows_o >> 2, n_kg = rows_k >> 2, n_micro = n_og * n_kg;
+  const int n_steps = 3 * (TP >> 2);                  // (stream, 4-point group) steps
+  const int rounds = (n_micro * split + blockDim.x - 1) / blockDim.x;
+  for (int r = 0; r < rounds; ++r) {
+    const int mt = r * blockDim.x + threadIdx.x;
+    const bool active = mt < n_micro * split;
+    const int half = active ? mt / n_micro : 0, m = active ? mt % n_micro : 0;
+    const int kg = m % n_kg, og = m / n_kg;
+    const int s0 = half * n_steps / split, s1 = (half + 1) * n_steps / split;
     R acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = (R)0;
-    for (int s = 0; s < 3; ++s) {
-      const R* Zs = Zb + s * plane;
-      const R* Hs = H + s * plane;
-      for (int p = 0; p < TP; p += 4) {
+    if (active)
+      for (int st = s0; st < s1; ++st) {
+        const int sstream = st / (TP >> 2), p = (st % (TP >> 2)) << 2;
+        const R* Zs = Zb + sstream * plane;
+        const R* Hs = H + sstream * plane;
         R z[4][4], h[4][4];
 #pragma unroll
         for (int oo = 0; oo < 4; ++oo) ld4(Zs + (og + oo * n_og) * TPS + p, z[oo]);
@@ -323,14 +410,24 @@ __device__ void wgrad_layer(const R* __restrict__ Zb, const R* __restrict__ H, i
 #pragma unroll
             for (int pp = 0; pp < 4; ++pp) acc[oo][kk] = fma(z[oo][pp], h[kk][pp], acc[oo][kk]);
       }
+    if (split > 1) {
+      if (active && half == 1)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) scratch[m * 16 + i] = acc[i >> 2][i & 3];
+      __syncthreads();
+      if (active && half == 0)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i >> 2][i & 3] += scratch[m * 16 + i];
+      __syncthreads();
     }
+    if (active && half == 0)
 #pragma unroll
-    for (int oo = 0; oo < 4; ++oo)
+      for (int oo = 0; oo < 4; ++oo)
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const int o = og + oo * n_og, k = kg + kk * n_kg;
-        if (o < out && k < in) G.add(off + o * in + k, acc[oo][kk]);
-      }
+        for (int kk = 0; kk < 4; ++kk) {
+          const int o = og + oo * n_og, k = kg + kk * n_kg;
+          if (o < out && k < in) G.add(off + o * in + k, acc[oo][kk]);
+        }
   }
 }
 
@@ -355,30 +452,30 @@ __device__ void bgrad(const R* __restrict__ Zb, int out, int TP, int TPS, GradAc
   }
 }
 
-// Tb[s][k][p] = sum_o W[o][k] Zb[s][o][p]; 4x4 (k, p) micro-tiles.
-template <class R>
+// Tb[s][k][p] = sum_o W[o][k] Zb[s][o][p]; 4 x PP (k, p) micro-tiles.
+template <class R, int PP = 4>
 __device__ void tbar_layer(const R* __restrict__ W, int ld, int out, int rows_k, const R* __restrict__ Zb,
                            R* __restrict__ Tb, int TP, int TPS, int plane) {
-  const int n_pg = TP >> 2, n_kg = rows_k >> 2;
+  const int n_pg = TP / PP, n_kg = rows_k >> 2;
   for (int mt = threadIdx.x; mt < n_kg * n_pg; mt += blockDim.x) {
-    const int pg = mt % n_pg, kg = mt / n_pg, p0 = pg << 2, k0 = kg << 2;
-    R acc[3][4][4];
+    const int pg = mt % n_pg, kg = mt / n_pg, p0 = pg * PP, k0 = kg << 2;
+    R acc[3][4][PP];
 #pragma unroll
     for (int s = 0; s < 3; ++s)
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[s][i][j] = (R)0;
+        for (int j = 0; j < PP; ++j) acc[s][i][j] = (R)0;
     for (int o = 0; o < out; ++o) {
-      R w[4], z0[4], z1[4], z2[4];
+      R w[4], z0[PP], z1[PP], z2[PP];
       ld4(W + o * ld + k0, w);
-      ld4(Zb + o * TPS + p0, z0);
-      ld4(Zb + plane + o * TPS + p0, z1);
-      ld4(Zb + 2 * plane + o * TPS + p0, z2);
+      ldp<PP>(Zb + o * TPS + p0, z0);
+      ldp<PP>(Zb + plane + o * TPS + p0, z1);
+      ldp<PP>(Zb + 2 * plane + o * TPS + p0, z2);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) {
+        for (int pp = 0; pp < PP; ++pp) {
           acc[0][kk][pp] = fma(w[kk], z0[pp], acc[0][kk][pp]);
           acc[1][kk][pp] = fma(w[kk], z1[pp], acc[1][kk][pp]);
           acc[2][kk][pp] = fma(w[kk], z2[pp], acc[2][kk][pp]);
@@ -386,28 +483,29 @@ __device__ void tbar_layer(const R* __restrict__ W, int ld, int out, int rows_k,
     }
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-      st4(Tb + (k0 + kk) * TPS + p0, acc[0][kk]);
-      st4(Tb + plane + (k0 + kk) * TPS + p0, acc[1][kk]);
-      st4(Tb + 2 * plane + (k0 + kk) * TPS + p0, acc[2][kk]);
+      stp<PP>(Tb + (k0 + kk) * TPS + p0, acc[0][kk]);
+      stp<PP>(Tb + plane + (k0 + kk) * TPS + p0, acc[1][kk]);
+      stp<PP>(Tb + 2 * plane + (k0 + kk) * TPS + p0, acc[2][kk]);
     }
   }
 }
 
 template <class R>
-__global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
+__global__ void __launch_bounds__(kThreadsBwd) mlp_bwd_simt(BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const MlpShape& sh = a.sh;
   const WLayout& wl = a.wl;
   const int L = sh.L, TP = a.TP, TPS = a.TPS;
   const int plane = a.DP * TPS;
   GradAcc<R> G;
-  G.a = reinterpret_cast<decltype(G.a)>(smem);                     // [n_params] 8-byte entries (rounded to even)
-  R* sW = reinterpret_cast<R*>(smem + 8 * (size_t)((sh.n_params + 1) & ~1));
+  G.a = reinterpret_cast<R*>(smem);                               // [n_params] (rounded up to 4)
+  R* sW = G.a + ((sh.n_params + 3) & ~3);
   R* S = sW + wl.total;                                           // [L-1][3][DP][TPS]
   R* Zb = S + (size_t)(L - 1) * 3 * plane;
   R* Tb = Zb + 3 * plane;
   R* sX = Tb + 3 * plane;                                         // [2][TPS]
   R* sSeed = sX + 2 * TPS;                                        // [4][TPS]: u, u_x, u_y (, eps) seeds
+  R* sScr = sSeed + 4 * TPS;                                      // weight-gradient halves [micro-tiles][16]
   const bool two = sh.w[L] == 2;
   for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) G.zero(i);
   load_weights<R>(sh, wl, reinterpret_cast<const R*>(a.params), sW);
@@ -430,8 +528,15 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
     fwd_layer0<R>(sW + wl.woff[0], sW + wl.boff[0], wl.ld[0], wl.rows[0], sX, S, TP, TPS, plane);
     __syncthreads();
     for (int i = 1; i < L - 1; ++i) {
-      fwd_layer<R>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i], S + (size_t)(i - 1) * 3 * plane,
-                   S + (size_t)i * 3 * plane, TP, TPS, plane);
+      if (a.pp == 1)
+        fwd_layer<R, 1>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i],
+                        S + (size_t)(i - 1) * 3 * plane, S + (size_t)i * 3 * plane, TP, TPS, plane);
+      else if (a.pp == 2)
+        fwd_layer<R, 2>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i],
+                        S + (size_t)(i - 1) * 3 * plane, S + (size_t)i * 3 * plane, TP, TPS, plane);
+      else
+        fwd_layer<R>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i], wl.rows[i], S + (size_t)(i - 1) * 3 * plane,
+                     S + (size_t)i * 3 * plane, TP, TPS, plane);
       __syncthreads();
     }
     // output layer: gradient of w_L, b_L and seeds for the last hidden layer; a
@@ -480,11 +585,16 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
       __syncthreads();
       const int goff = sh.off[i];
       if (i >= 1)
-        wgrad_layer<R>(Zb, S + (size_t)(i - 1) * 3 * plane, out, in, wl.rows[i], wl.ld[i], TP, TPS, plane, G, goff);
+        wgrad_layer<R>(Zb, S + (size_t)(i - 1) * 3 * plane, out, in, wl.rows[i], wl.ld[i], TP, TPS, plane, G, goff,
+                       a.wsplit, sScr);
       else
         wgrad_layer0<R>(Zb, sX, out, TP, TPS, plane, G, goff);
       bgrad<R>(Zb, out, TP, TPS, G, goff + out * in);
-      if (i >= 1) tbar_layer<R>(sW + wl.woff[i], wl.ld[i], out, wl.ld[i], Zb, Tb, TP, TPS, plane);
+      if (i >= 1) {
+        if (a.pp == 1) tbar_layer<R, 1>(sW + wl.woff[i], wl.ld[i], out, wl.ld[i], Zb, Tb, TP, TPS, plane);
+        else if (a.pp == 2) tbar_layer<R, 2>(sW + wl.woff[i], wl.ld[i], out, wl.ld[i], Zb, Tb, TP, TPS, plane);
+        else tbar_layer<R>(sW + wl.woff[i], wl.ld[i], out, wl.ld[i], Zb, Tb, TP, TPS, plane);
+      }
       __syncthreads();
     }
   }
@@ -493,15 +603,16 @@ __global__ void __launch_bounds__(kThreads) mlp_bwd_simt(BwdArgs a) {
   for (int i = threadIdx.x; i < sh.n_params; i += blockDim.x) dst[i] = G.get(i);
 }
 
-size_t fwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rsz) {
+size_t fwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rsz, bool inplace = false) {
   const int TPS = tps_for(TP);
-  return rsz * ((size_t)wl.total + 6 * (size_t)DP * TPS + 2 * TPS);
+  return rsz * ((size_t)wl.total + (inplace ? 3 : 6) * (size_t)DP * TPS + 2 * TPS);
 }
 
 size_t bwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rsz) {
   const int TPS = tps_for(TP);
-  size_t b = 8 * (size_t)((sh.n_params + 1) & ~1);
+  size_t b = rsz * (size_t)((sh.n_params + 3) & ~3);
   b += rsz * ((size_t)wl.total + (size_t)(sh.L - 1) * 3 * DP * TPS + 6 * (size_t)DP * TPS + 6 * TPS);
+  b += rsz * (size_t)(DP / 4) * (DP / 4) * 16;   // weight-gradient halves
   return b;
 }
 
@@ -510,8 +621,8 @@ int pick_tp_bwd(fv_ctx ctx, const MlpShape& sh, const WLayout& wl, int DP, size_
   int best = 0;
   for (int TP = 4; TP <= 64; TP += 4)
     if (bwd_smem(sh, wl, DP, TP, rsz) <= budget) best = TP;
-  // prefer TP that fills the 4x4 micro-tile grid without huge tiles
-  return std::min(best, 32);
+  // prefer TP that fills the micro-tile grid without huge tiles
+  return std::min(best, 40);
 }
 
 template <class R>
@@ -521,8 +632,12 @@ int launch_fwd_t(fv_ctx ctx, const EvalPlan& pl, const void* params, const doubl
   a.wl = make_layout(pl.shape);
   a.DP = max_hidden_pad(pl.shape);
   a.TP = sizeof(R) == 8 ? 32 : 64;
-  size_t smem = fwd_smem(a.sh, a.wl, a.DP, a.TP, sizeof(R));
-  while (smem > ctx->smem_optin && a.TP > 4) { a.TP -= 4; smem = fwd_smem(a.sh, a.wl, a.DP, a.TP, sizeof(R)); }
+  // in place when every hidden map's micro-tiles fit one per thread
+  int max_micro = 0;
+  for (int i = 1; i < a.sh.L - 1; ++i) max_micro = std::max(max_micro, (a.wl.rows[i] / 4) * (a.TP / 4));
+  a.inplace = max_micro <= kThreads;
+  size_t smem = fwd_smem(a.sh, a.wl, a.DP, a.TP, sizeof(R), a.inplace);
+  while (smem > ctx->smem_optin && a.TP > 4) { a.TP -= 4; smem = fwd_smem(a.sh, a.wl, a.DP, a.TP, sizeof(R), a.inplace); }
   if (smem > ctx->smem_optin) { set_error("network too large for the shared-memory forward kernel"); return FV_ERR_UNSUPPORTED; }
   a.TPS = tps_for(a.TP);
   a.params = params; a.Xm = Xm; a.P_mesh = pl.P_mesh; a.Xe = Xe; a.P_tot = pl.P_tot; a.U = U;
@@ -546,6 +661,12 @@ int bwd_config(fv_ctx ctx, const EvalPlan& pl, BwdArgs* a, size_t* smem, int* gr
   a->TP = pick_tp_bwd(ctx, a->sh, a->wl, a->DP, sizeof(R));
   if (a->TP == 0) { set_error("network too large for the shared-memory reverse kernel"); return FV_ERR_UNSUPPORTED; }
   a->TPS = tps_for(a->TP);
+  // micro-tile shapes that keep most of the CTA's threads busy
+  const int n_og = a->DP / 4;
+  a->pp = 4;
+  if (n_og * (a->TP / 4) * 2 <= kThreadsBwd && a->TP % 2 == 0) a->pp = 2;
+  if (n_og * (a->TP / 2) * 2 <= kThreadsBwd) a->pp = 1;
+  a->wsplit = n_og * n_og * 2 <= kThreadsBwd ? 2 : 1;
   *smem = bwd_smem(a->sh, a->wl, a->DP, a->TP, sizeof(R));
   const int64_t n_tiles = (pl.P_tot + a->TP - 1) / a->TP;
   const int per_sm = std::max<int>(1, (int)(std::min<size_t>(ctx->smem_optin, 228 * 1024) / (*smem + 1024)));
@@ -565,7 +686,7 @@ int launch_bwd_t(fv_ctx ctx, const EvalPlan& pl, const void* params, const doubl
   *nb = grid;
   cudaError_t e = ensure_smem_attr(ctx, (const void*)mlp_bwd_simt<R>, smem);
   if (e == cudaSuccess) {
-    mlp_bwd_simt<R><<<grid, kThreads, smem, ctx->stream>>>(a);
+    mlp_bwd_simt<R><<<grid, kThreadsBwd, smem, ctx->stream>>>(a);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) { set_error("mlp reverse launch failed: %s", cudaGetErrorString(e)); return FV_ERR_CUDA; }
