@@ -110,15 +110,18 @@ const char* fv_last_error(void);
  * counts per kernel kind (names: fv_kernel_name).  Off by default. */
 int fv_ctx_enable_timing(fv_ctx ctx, int on);
 
-/* Activation stash of the tensor-core reverse sweep (FV_BF16 / FV_FP16
- * gradients of networks with 3 or 4 hidden layers), on by default: the
- * forward kernel also writes, per 128-point tile, the hidden activations of
- * the layers below the last hidden map (value and both tangents, 16-bit, 384
- * bytes per point and layer at width 50) to the context's workspace, and the
- * reverse kernel reads them by bulk copies instead of recomputing those maps
- * (Sec. 4.4's tensor form of the loss; the reverse sweep of the network in
- * Eq. NN).  Off: the reverse kernel recomputes them.  Results are bitwise the
- * same either way.  A fixed scratch area too small for it (fv_loss_grad_noalloc)
+/* Activation stash of the reverse sweep, on by default: the forward kernel
+ * also writes each tile's hidden activations (value and both tangents) to the
+ * context's workspace, and the reverse kernel reads them by bulk copies
+ * instead of recomputing those maps (Sec. 4.4's tensor form of the loss; the
+ * reverse sweep of the network in Eq. NN).
+ *   FV_BF16 / FV_FP16 gradients of networks with 3 or 4 hidden layers: the
+ *     layers below the last hidden map, 16-bit, per 128-point tile (384 bytes
+ *     per point and layer at width 50).
+ *   FV_FP32 / FV_FP64: every hidden layer, in the path's precision, per tile
+ *     of the reverse kernel (about 2.5 KB per point in FP32 at width 50x4).
+ * Off: the reverse kernel recomputes them.  Results are bitwise the same
+ * either way.  A fixed scratch area too small for it (fv_loss_grad_noalloc)
  * or a workspace allocation that fails with it falls back to recomputing.
  * Errors: FV_ERR_ARG (null context). */
 int fv_ctx_set_activation_stash(fv_ctx ctx, int on);

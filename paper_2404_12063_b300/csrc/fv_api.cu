@@ -368,9 +368,9 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   w.gpart = o; o += al((size_t)nb * sh.n_params * 8);
   w.smax = o; o += al(16);
   w.ctr = o; o += al(16);
-  // activation stash of the tensor-core reverse sweep; left out (the reverse
+  // activation stash of the reverse sweep; left out (the reverse
   // kernel recomputes) when a fixed scratch area has no room for it
-  size_t stash_bytes = tc && want_grad && ctx->tc_stash ? mlp_tc_stash_bytes(pl) : 0;
+  size_t stash_bytes = !want_grad || !ctx->tc_stash ? 0 : tc ? mlp_tc_stash_bytes(pl) : mlp_simt_stash_bytes(ctx, pl);
   if (fixed_ws && o + al(stash_bytes) > fixed_ws_bytes) stash_bytes = 0;
   w.stash = o; o += al(stash_bytes);
   w.total = o;
@@ -407,7 +407,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   const double* Xe = bc ? bc->xy : nullptr;
 
   rc = tc ? launch_mlp_fwd_tc(ctx, pl, params, mesh->X, Xe, U, tile_ctr, stash)
-          : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U);
+          : launch_mlp_fwd(ctx, pl, params, mesh->X, Xe, U, stash);
   if (rc) return rc;
   const double inv_norm = 1.0 / (opts->norm == FV_NORM_TEST ? mesh->Nt : mesh->n_e);
   // Boundary and sensor terms read U and write the boundary points' seeds and
@@ -455,7 +455,7 @@ int evaluate(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, fv_bc bc, const fv_ml
   int ngp = 0;
   if (want_grad) {
     rc = tc ? launch_mlp_bwd_tc(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp, smax, stash)
-            : launch_mlp_bwd(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp);
+            : launch_mlp_bwd(ctx, pl, params, mesh->X, Xe, UB, gpart, &ngp, stash);
     if (rc) return rc;
   }
   cudaEvent_t ta;

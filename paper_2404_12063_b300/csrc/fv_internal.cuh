@@ -71,7 +71,7 @@ struct fv_ctx_s {
   cudaStream_t stream = nullptr;
   int n_sm = 148;
   int tc_ctas_cap = 0;              // > 0: at most this many tensor-core MLP CTAs per SM (kernels sharing the GPU)
-  bool tc_stash = true;             // tensor-core reverse sweep reads stored activations (false: recomputes them)
+  bool tc_stash = true;             // reverse sweeps read stored activations (false: recompute them)
   size_t smem_optin = 227 * 1024;
   size_t smem_per_sm = 228 * 1024;
   fv::Workspace ws;
@@ -240,8 +240,12 @@ __device__ __forceinline__ void warp_max_to(float* word, float v) {
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(word, v);
 }
 
+// stash: null, or mlp_simt_stash_bytes(ctx, pl) bytes that the forward fills
+// with the hidden layers (value and tangents) the reverse sweep then reads
+// instead of recomputing them.
 int launch_mlp_fwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
-                   void* U);
+                   void* U, void* stash = nullptr);
+size_t mlp_simt_stash_bytes(fv_ctx ctx, const EvalPlan& pl);   // 0: no stash for this network
 int autotune_contract(fv_ctx ctx, fv_mesh mesh, fv_precision prec, double* ms_out);
 int launch_contract_mfree(fv_ctx ctx, fv_mesh mesh, fv_forcing forcing, const EvalPlan& pl, const void* U,
                           void* UB, double eps, const double* eps_dev, double bx, double by, double rscale,
@@ -261,7 +265,7 @@ int contract_grid(fv_ctx ctx, fv_mesh mesh, fv_precision prec, int* grid, int* e
                   size_t* smem, bool matrix_free = false);
 int launch_bc(fv_ctx ctx, fv_bc bc, const EvalPlan& pl, const void* U, void* UB, double* partial2);
 int launch_mlp_bwd(fv_ctx ctx, const EvalPlan& pl, const void* params, const double* Xmesh, const double* Xextra,
-                   const void* UB, double* gpart, int* n_blocks_out);
+                   const void* UB, double* gpart, int* n_blocks_out, const void* stash = nullptr);
 int mlp_bwd_blocks(fv_ctx ctx, const EvalPlan& pl);
 int launch_finalize(fv_ctx ctx, const EvalPlan& pl, const double* cpart, int n_cpart, const double* bcpart,
                     const double* gpart, int n_gpart, double inv_norm, double tau, double gamma, int n_bd, int n_s,

@@ -70,6 +70,27 @@ def oracle_eval(prob, params64, norm=0, **kw):
     return oracle.Bound(prob, norm=norm).loss_grad(params64, n_threads=NTH, **kw)
 
 
+def deps_scale(prob, params64, norm):
+    """Magnitude against which an error of dL/deps is measured when dL/deps
+    cancels.  With R_ej = eps A_ej + V_ej - F_ej (the variational residual:
+    A = sum_q Gx u_x + Gy u_y, V = sum_q Gv (b . grad u)) and
+    dL/deps = (2/N) sum_ej R_ej A_ej, a relative perturbation eta of grad u at
+    every quadrature point moves dL/deps by at most
+    eta (2/N) sum_ej (|R_ej| Abar_ej + |A_ej| (eps Abar_ej + Vbar_ej)),
+    Abar, Vbar the same sums over absolute values.  That sum (times eta = the
+    path's relative tolerance) is the error FP32 rounding of grad u alone can
+    cause, however well the rest is computed."""
+    B = oracle.Bound(prob, norm=norm)
+    ref = B.loss_grad(params64, want_grad=False, want_R=True, want_upts=True, n_threads=NTH)
+    Gx, Gy, Gv, _ = B.tensors()
+    ux, uy = ref["upts"][..., 1], ref["upts"][..., 2]
+    A = np.einsum("ejq,eq->ej", Gx, ux) + np.einsum("ejq,eq->ej", Gy, uy)
+    Ab = np.einsum("ejq,eq->ej", np.abs(Gx), np.abs(ux)) + np.einsum("ejq,eq->ej", np.abs(Gy), np.abs(uy))
+    Vb = np.einsum("ejq,eq->ej", np.abs(Gv), abs(prob.b[0]) * np.abs(ux) + abs(prob.b[1]) * np.abs(uy))
+    n = prob.test_order ** 2 if norm == 0 else prob.mesh.cells.shape[0]
+    return 2.0 / n * np.sum(np.abs(ref["R"]) * Ab + np.abs(A) * (prob.eps * Ab + Vb))
+
+
 def check_against_oracle(api, ctx, prob, precision, storage=None, norm="test", tol=None, tol_lv=None, g_mode=None):
     tol = TOL[precision] if tol is None else tol
     tol_lv = tol if tol_lv is None else tol_lv
@@ -85,7 +106,11 @@ def check_against_oracle(api, ctx, prob, precision, storage=None, norm="test", t
     assert rel(grad, ref["grad"]) < tol, rel(grad, ref["grad"])
     if prob.eps != 1.0 or prob.b != (0.0, 0.0):
         if precision in ("fp64", "fp32"):
-            assert rel(out[4], ref["dL_deps"]) < tol, (out[4], ref["dL_deps"])
+            # relative error of dL/deps itself, or, where dL/deps cancels,
+            # measured against what rounding of grad u alone can move it by
+            err = abs(out[4] - ref["dL_deps"])
+            if err > tol * abs(ref["dL_deps"]):
+                assert err <= tol * deps_scale(prob, p64, 0 if norm == "test" else 1), (out[4], ref["dL_deps"])
         # eps is one more trainable coordinate: its derivative is judged as part
         # of the (theta, eps) gradient vector, norm-wise.  (At the start point it
         # is a strongly cancelling sum, so its own relative error under BF16
@@ -684,6 +709,26 @@ def test_activation_stash_equals_recompute(api, ctx, widths, precision):
     if widths is not None:
         prob = _with(prob, widths=widths, params=fi.random_bias_params(widths, 5, 1))
     pb = api.problem_from_inputs(ctx, prob, precision, "bf16")
+    params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+    try:
+        ctx.set_activation_stash(True)
+        o1, g1 = pb.loss_grad(params)
+        o1, g1 = o1.clone(), g1.clone()
+        ctx.set_activation_stash(False)
+        o2, g2 = pb.loss_grad(params)
+    finally:
+        ctx.set_activation_stash(True)
+    assert torch.equal(o1, o2) and torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("k,precision", [("annulus", "fp32"), ("disc", "fp64"), ("tiny", "fp32"), ("eps_disc", "fp32")])
+def test_cuda_core_activation_stash_equals_recompute(api, ctx, k, precision):
+    """FP32/FP64 path: the reverse sweep that bulk-loads the forward kernel's
+    stored hidden layers returns bitwise what recomputing them gives (the
+    annulus: 25,600 tiles of 32 points, so each CTA requests its next tile's
+    layers while it sweeps the current one; eps_disc: a two-output network)."""
+    prob = fi.eps_field_disc() if k == "eps_disc" else cfg(k)
+    pb = api.problem_from_inputs(ctx, prob, precision)
     params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
     try:
         ctx.set_activation_stash(True)
