@@ -725,8 +725,9 @@ def test_activation_stash_equals_recompute(api, ctx, widths, precision):
 def test_cuda_core_activation_stash_equals_recompute(api, ctx, k, precision):
     """FP32/FP64 path: the reverse sweep that bulk-loads the forward kernel's
     stored hidden layers returns bitwise what recomputing them gives (the
-    annulus: 25,600 tiles of 32 points, so each CTA requests its next tile's
-    layers while it sweeps the current one; eps_disc: a two-output network)."""
+    annulus: about 23,000 tiles of 36 points, so each CTA requests its next
+    tile's layers while it sweeps the current one; eps_disc: a two-output
+    network)."""
     prob = fi.eps_field_disc() if k == "eps_disc" else cfg(k)
     pb = api.problem_from_inputs(ctx, prob, precision)
     params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
