@@ -259,6 +259,23 @@ template <class R> struct PointsPerTile { static constexpr int v = sizeof(R) == 
 // maps to (row-group pair, point group) with the point group fastest, so the
 // eight pairs of a half-warp read eight different 16-byte chunks of one row.
 
+// Pair index q -> (row-group pair, point group).  Point groups go in blocks
+// of eight (the eight pairs of a half-warp read eight chunks of one row, in
+// distinct bank groups); the groups past the last full block of eight are
+// spread over the row-group pairs on their own, so no half-warp reads two
+// chunks eight apart (which share banks).
+__device__ __forceinline__ void pair_split(int q, int n_pg, int n_rgp, int& pg, int& rgp) {
+  const int full = n_pg & ~7, rem = n_pg - full;
+  if (q < n_rgp * full || rem == 0) {
+    pg = q % full;
+    rgp = q / full;
+  } else {
+    const int r = q - n_rgp * full;
+    pg = full + r % rem;
+    rgp = r / rem;
+  }
+}
+
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -268,12 +285,15 @@ __device__ __forceinline__ void named_sync(int id, int n) {
 // o = og + n_og*oo (oo < 4), points p0..p0+PW-1, three streams; the lanes of
 // a pair share the points (og = 2 x pair row group + lane parity); k runs
 // over the padded inputs four at a time (padded weight columns are zero, so
-// the constant row adds nothing).  The k range of a tile is split between
+// the constant row adds nothing).  SPLIT: point groups as in pair_split (the
+// forward kernel: 3.5% faster), else point group fastest (the reverse
+// kernel's recompute path; either gives each element the same arithmetic,
+// only the thread that computes it differs).  The k range of a tile is split between
 // two threads in different warps of one scheduler: the second leaves its
 // partial sums in B at the tile's own places, and after a CTA barrier the
 // first adds them and applies the tanh rule.  Every thread of the CTA calls
 // this (barriers).
-template <class R, int PW>
+template <class R, int PW, bool SPLIT>
 __device__ void fwd_gemm(const R* __restrict__ W, const R* __restrict__ b, int ld, int out, int rows,
                          const R* __restrict__ A, R* __restrict__ B, int TP, int TPS, int plane) {
   const int n_og = rows >> 2, n_pg = TP / PW, slots = 2 * ((n_og + 1) >> 1) * n_pg;
@@ -282,7 +302,14 @@ __device__ void fwd_gemm(const R* __restrict__ W, const R* __restrict__ b, int l
   const int k0 = half ? kh : 0, k1 = half ? ld : kh;
   for (int base = 0; base < slots; base += T) {
     const int q2 = base + threadIdx.x - half * T, q = q2 >> 1;
-    const int pg = q % n_pg, og = 2 * (q / n_pg) + (q2 & 1), p0 = pg * PW;
+    int pg, ogp;
+    if (SPLIT) {
+      pair_split(q, n_pg, (n_og + 1) >> 1, pg, ogp);
+    } else {
+      pg = q % n_pg;
+      ogp = q / n_pg;
+    }
+    const int og = 2 * ogp + (q2 & 1), p0 = pg * PW;
     const bool active = q2 < slots && og < n_og;
     using P = typename PairOf<R>::T;
     constexpr int NP = PW / 2;
@@ -381,6 +408,7 @@ __device__ void tbar_gemm(const R* __restrict__ W, int ld, int out, int krows, c
                           int nthr) {
   const int n_kg = krows >> 2, n_pg = TP / PW, n_pairs = ((n_kg + 1) >> 1) * n_pg;
   for (int q2 = tid; q2 < 2 * n_pairs; q2 += nthr) {
+    // (point group fastest; the split of pair_split measured no faster here)
     const int q = q2 >> 1, pg = q % n_pg, kg = 2 * (q / n_pg) + (q2 & 1), p0 = pg * PW, k0 = kg << 2;
     if (kg >= n_kg) continue;
     using P = typename PairOf<R>::T;
@@ -639,7 +667,8 @@ __global__ void __launch_bounds__(kThreads) mlp_fwd_simt(FwdArgs a) {
         if (lead) tc::bulk_wait_read<1>();
         __syncthreads();
       }
-      fwd_gemm<R, PW>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i + 1], wl.rows[i], A, B, TP, TPS, plane);
+      fwd_gemm<R, PW, true>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i + 1], wl.rows[i], A, B, TP, TPS,
+                            plane);
       if (stash && lead) tc::bulk_store(st_tile + (size_t)i * slot_bytes, B, slot_bytes);
       R* t = A; A = B; B = t;
     }
@@ -756,7 +785,7 @@ __global__ void __launch_bounds__(kThreadsBwd) mlp_bwd_simt(BwdArgs a) {
       fwd_layer0<R, PW>(sW + wl.woff[0], sW + wl.boff[0], wl.ld[0], sh.w[1], wl.rows[0], sX, S, TP, TPS, plane);
       __syncthreads();
       for (int i = 1; i < L - 1; ++i) {
-        fwd_gemm<R, PW>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i + 1], wl.rows[i],
+        fwd_gemm<R, PW, false>(sW + wl.woff[i], sW + wl.boff[i], wl.ld[i], sh.w[i + 1], wl.rows[i],
                         S + (size_t)(i - 1) * 3 * plane, S + (size_t)i * 3 * plane, TP, TPS, plane);
         __syncthreads();
       }
