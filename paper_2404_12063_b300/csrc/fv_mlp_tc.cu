@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
       wait_mma();
     }
     {
-      const int Nout = tb->WP[last], wo = tb->w[last + 1];
+      const int Nout = tb->WP[last];
       if (c0 < Nout) {
 #pragma unroll
         for (int sc8 = 0; sc8 < 16; sc8 += 8) {
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(tc_threads<HP>(), HP == 32 ? 2 : 1) mlp_bwd_tc
             float zv[2], zx[2], zy[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              // the bias column (o == wo) has zero weights into it and a zero output
+              // the bias column (o == w[last + 1]) has zero weights into it and a zero output
               // weight: its t, tangents and adjoints come out 0 here; only the
               // output-bias gradient needs its value 1, added below
               const int o = cc + j + h;
