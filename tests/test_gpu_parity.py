@@ -742,6 +742,28 @@ def test_cuda_core_activation_stash_equals_recompute(api, ctx, k, precision):
     assert torch.equal(o1, o2) and torch.equal(g1, g2)
 
 
+@pytest.mark.parametrize("widths", [[2, 16, 8, 32, 1], [2, 12, 12, 12, 12, 12, 12, 1], [2, 48, 1]])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_cuda_core_widths_and_depths(api, ctx, widths, precision):
+    """CUDA-core path on widths that are multiples of four (the constant-1 bias
+    row then takes a padding group of its own), six hidden layers (six stash
+    slots) and one hidden layer (no hidden-to-hidden map): against the oracle,
+    and stash on / off bitwise equal."""
+    prob = _with(cfg("disc"), widths=widths, params=fi.random_bias_params(widths, 3, 1))
+    check_against_oracle(api, ctx, prob, precision)
+    pb = api.problem_from_inputs(ctx, prob, precision)
+    params = torch.tensor(prob.params, dtype=pb.dtype, device="cuda")
+    try:
+        ctx.set_activation_stash(True)
+        o1, g1 = pb.loss_grad(params)
+        o1, g1 = o1.clone(), g1.clone()
+        ctx.set_activation_stash(False)
+        o2, g2 = pb.loss_grad(params)
+    finally:
+        ctx.set_activation_stash(True)
+    assert torch.equal(o1, o2) and torch.equal(g1, g2)
+
+
 def test_fp16_tighter_than_bf16(api, ctx):
     """The FP16 operand path is measurably closer to the oracle than BF16."""
     prob = cfg("annulus")
