@@ -348,40 +348,81 @@ __device__ void fwd_gemm(const R* __restrict__ W, const R* __restrict__ b, int l
         }
       }
     }
-    if (active && half == 1)
+    if constexpr (SPLIT) {
+      // each half finishes two of the four row groups (adds the other half's
+      // partial sums and applies the tanh rule), sharing the epilogue's tanh
+      // work; a row's value is (first half + second half) + bias as below
+      auto finishes = [&](int oo) { return (oo >> 1) == half; };
 #pragma unroll
-      for (int oo = 0; oo < 4; ++oo) {
-        R* Bo = B + (og + oo * n_og) * TPS + p0;
+      for (int oo = 0; oo < 4; ++oo)
+        if (active && !finishes(oo)) {
+          R* Bo = B + (og + oo * n_og) * TPS + p0;
 #pragma unroll
-        for (int s = 0; s < 3; ++s)
+          for (int s = 0; s < 3; ++s)
 #pragma unroll
-          for (int j = 0; j < NP; ++j) reinterpret_cast<P*>(Bo + s * plane)[j] = acc[s][oo][j];
-      }
-    __syncthreads();
-    if (active && half == 0)
-#pragma unroll
-      for (int oo = 0; oo < 4; ++oo) {
-        const int o = og + oo * n_og;
-        R* Bo = B + o * TPS + p0;
-        R q0[PW], q1[PW], qq2[PW];
-        ldp<PW>(Bo, q0);
-        ldp<PW>(Bo + plane, q1);
-        ldp<PW>(Bo + 2 * plane, qq2);
-        const R bo = b[o];
-        const bool one = o == out;
-        R t4[PW], x4[PW], y4[PW];
-#pragma unroll
-        for (int pp = 0; pp < PW; ++pp) {
-          const P c0 = acc[0][oo][pp >> 1], c1 = acc[1][oo][pp >> 1], c2 = acc[2][oo][pp >> 1];
-          const R t = tanh_r(((pp & 1) ? c0.y : c0.x) + q0[pp] + bo), sd = (R)1 - t * t;
-          t4[pp] = one ? (R)1 : t;
-          x4[pp] = one ? (R)0 : sd * (((pp & 1) ? c1.y : c1.x) + q1[pp]);
-          y4[pp] = one ? (R)0 : sd * (((pp & 1) ? c2.y : c2.x) + qq2[pp]);
+            for (int j = 0; j < NP; ++j) reinterpret_cast<P*>(Bo + s * plane)[j] = acc[s][oo][j];
         }
-        stp<PW>(Bo, t4);
-        stp<PW>(Bo + plane, x4);
-        stp<PW>(Bo + 2 * plane, y4);
-      }
+      __syncthreads();
+#pragma unroll
+      for (int oo = 0; oo < 4; ++oo)
+        if (active && finishes(oo)) {
+          const int o = og + oo * n_og;
+          R* Bo = B + o * TPS + p0;
+          R q0[PW], q1[PW], qq2[PW];
+          ldp<PW>(Bo, q0);
+          ldp<PW>(Bo + plane, q1);
+          ldp<PW>(Bo + 2 * plane, qq2);
+          const R bo = b[o];
+          const bool one = o == out;
+          R t4[PW], x4[PW], y4[PW];
+#pragma unroll
+          for (int pp = 0; pp < PW; ++pp) {
+            const P c0 = acc[0][oo][pp >> 1], c1 = acc[1][oo][pp >> 1], c2 = acc[2][oo][pp >> 1];
+            const R t = tanh_r(((pp & 1) ? c0.y : c0.x) + q0[pp] + bo), sd = (R)1 - t * t;
+            t4[pp] = one ? (R)1 : t;
+            x4[pp] = one ? (R)0 : sd * (((pp & 1) ? c1.y : c1.x) + q1[pp]);
+            y4[pp] = one ? (R)0 : sd * (((pp & 1) ? c2.y : c2.x) + qq2[pp]);
+          }
+          stp<PW>(Bo, t4);
+          stp<PW>(Bo + plane, x4);
+          stp<PW>(Bo + 2 * plane, y4);
+        }
+    } else {
+      if (active && half == 1)
+#pragma unroll
+        for (int oo = 0; oo < 4; ++oo) {
+          R* Bo = B + (og + oo * n_og) * TPS + p0;
+#pragma unroll
+          for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int j = 0; j < NP; ++j) reinterpret_cast<P*>(Bo + s * plane)[j] = acc[s][oo][j];
+        }
+      __syncthreads();
+      if (active && half == 0)
+#pragma unroll
+        for (int oo = 0; oo < 4; ++oo) {
+          const int o = og + oo * n_og;
+          R* Bo = B + o * TPS + p0;
+          R q0[PW], q1[PW], qq2[PW];
+          ldp<PW>(Bo, q0);
+          ldp<PW>(Bo + plane, q1);
+          ldp<PW>(Bo + 2 * plane, qq2);
+          const R bo = b[o];
+          const bool one = o == out;
+          R t4[PW], x4[PW], y4[PW];
+#pragma unroll
+          for (int pp = 0; pp < PW; ++pp) {
+            const P c0 = acc[0][oo][pp >> 1], c1 = acc[1][oo][pp >> 1], c2 = acc[2][oo][pp >> 1];
+            const R t = tanh_r(((pp & 1) ? c0.y : c0.x) + q0[pp] + bo), sd = (R)1 - t * t;
+            t4[pp] = one ? (R)1 : t;
+            x4[pp] = one ? (R)0 : sd * (((pp & 1) ? c1.y : c1.x) + q1[pp]);
+            y4[pp] = one ? (R)0 : sd * (((pp & 1) ? c2.y : c2.x) + qq2[pp]);
+          }
+          stp<PW>(Bo, t4);
+          stp<PW>(Bo + plane, x4);
+          stp<PW>(Bo + 2 * plane, y4);
+        }
+    }
     tc::fence_proxy_async();   // B may be read next by a bulk copy
     __syncthreads();
   }
