@@ -774,8 +774,10 @@ __global__ void __launch_bounds__(kThreadsBwd) mlp_bwd_simt(BwdArgs a) {
   bool failed = false;
   auto arrive = [&](int i) {           // every thread: slot i holds the current tile's layer i
     const bool ok = tc::mbar_wait(&sbar[i], (sphase >> i) & 1u);
-    sphase ^= 1u << i;
-    if (threadIdx.x == 0) pending &= ~(1u << i);
+    if (ok) {                          // a copy that did not arrive stays pending (waited for at exit)
+      sphase ^= 1u << i;
+      if (threadIdx.x == 0) pending &= ~(1u << i);
+    }
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(a.err, FV_ERR_TIMEOUT);
       failed = true;
