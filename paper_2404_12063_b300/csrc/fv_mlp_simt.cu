@@ -244,6 +244,7 @@ __device__ void fwd_layer0(const R* W, const R* b, int ld, int out, int rows, co
 // (hbar = W^T zbar, fused with the tanh-rule adjoint of layer i-1) on the
 // first kTbarThreads threads and the weight-gradient GEMM on the rest.
 constexpr int kTbarThreads = 128;
+constexpr size_t kBwdStaticSmem = 1024;   // bound on the reverse kernel's static shared memory
 constexpr int kWgThreads = kThreadsBwd - kTbarThreads;
 constexpr int kWgBarrier = 1;   // named barrier of the weight-gradient threads
 
@@ -757,6 +758,7 @@ __global__ void __launch_bounds__(kThreadsBwd) mlp_bwd_simt(BwdArgs a) {
   // on barrier sbar[i]; the copy for the CTA's next tile is issued as soon as
   // the current tile has finished with the slot
   __shared__ uint64_t sbar[kMaxLayers];
+  static_assert(sizeof(sbar) <= kBwdStaticSmem, "static shared memory exceeds the reserve");
   const char* stash = static_cast<const char*>(a.stash);
   const uint32_t slot_bytes = (uint32_t)(3 * (size_t)plane * sizeof(R));
   const size_t tile_bytes = (size_t)(L - 1) * slot_bytes;
@@ -896,7 +898,9 @@ size_t bwd_smem(const MlpShape& sh, const WLayout& wl, int DP, int TP, size_t rs
 // groups; 36 measured 6% faster per step than 32, whose eight point groups
 // keep a half-warp's lane pairs in distinct banks).
 int pick_tp_bwd(fv_ctx ctx, const MlpShape& sh, const WLayout& wl, int DP, size_t rsz) {
-  const size_t budget = std::min<size_t>(ctx->smem_optin, 227 * 1024);
+  // the per-block limit covers the kernel's static shared memory (the stash
+  // barriers) as well as the dynamic part sized here
+  const size_t budget = std::min<size_t>(ctx->smem_optin, 227 * 1024) - kBwdStaticSmem;
   const int PW = rsz == 4 ? 4 : 2;
   int n_kg = 1;
   for (int i = 1; i < sh.L - 1; ++i) n_kg = std::max(n_kg, wl.ld[i] / 4);
